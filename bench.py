@@ -1,0 +1,353 @@
+"""Benchmark of the GB300 channelizer (arXiv 1411.0436 hot path).
+
+One step = one vspec_execute over one dump of the workload: dual-pol PFB,
+32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra of seeded synthetic
+int8 input resident in HBM. The metric is the real-time dual-polarisation
+bandwidth, S * N / t in GHz (complex sampling: one complex sample per
+polarisation per second of time is one hertz of bandwidth).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 the script runs under torchrun, one rank per GPU; every rank
+channelizes its own beam (independent input, no data exchange), so the work
+scales weakly. Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1411_0436_gb300 import workloads  # noqa: E402
+
+METRIC = "Dual-pol real-time bandwidth (GHz) & % HBM roofline, TC-FP16 vs FP32 FFT"
+CONFIG_NAME = "c2"
+WORKLOAD = ("dual-pol PFB, 32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra per dump, "
+            "int8 Gaussian sigma=20 with X/Y correlation 0.3 and two tones")
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1411_0436_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "vspec.h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, spectra_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return float(ent["dram_bytes_per_spectrum"]) * spectra_per_launch
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_rate(bank, x, budget_s: float, nthreads: int):
+    """Time the oracle on a bounded sample of the workload: GHz, spectra used."""
+    import oracle
+    oracle.build()
+    n = bank.nchan
+    t0 = time.perf_counter()
+    oracle.channelize(x, n, bank.ntaps, bank.npol, 4, bank.mode, bank.window, nthreads=nthreads)
+    per = (time.perf_counter() - t0) / 4
+    s = int(max(1, min(bank.nspectra, budget_s / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.channelize(x, n, bank.ntaps, bank.npol, s, bank.mode, bank.window, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return s * n / dt / 1e9, s, dt
+
+
+def run_reference(args, rank: int):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    bank = workloads.CONFIGS[CONFIG_NAME][0]
+    x = workloads.generate(bank, workloads.config_seed(CONFIG_NAME))
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = bank.nchan
+    t0 = time.perf_counter()
+    oracle.channelize(x, n, bank.ntaps, bank.npol, 2, bank.mode, bank.window, nthreads=threads)
+    per_spec = (time.perf_counter() - t0) / 2
+    step_budget = max(0.05, min(1.0, 150.0 / max(1, args.steps + args.warmup)))
+    s = int(max(1, min(bank.nspectra, step_budget / max(per_spec, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.channelize(x, n, bank.ntaps, bank.npol, s, bank.mode, bank.window, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.channelize(x, n, bank.ntaps, bank.npol, s, bank.mode, bank.window, nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * s * n / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GHz",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nchan": n, "ntaps": bank.ntaps, "npol": bank.npol,
+                   "nspectra_per_step": s},
+        "cpu_baseline": {"value": value, "unit": "GHz", "cores": threads, "kind": "oracle",
+                         "sample": f"first {s} spectra of the {CONFIG_NAME} input per step"},
+        "e2e": {"value": value, "unit": "GHz", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_1411_0436_gb300.vspec import Plan
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    bank = workloads.CONFIGS[CONFIG_NAME][0]
+    # each rank is an independent beam: its own seeded input
+    x = workloads.generate(bank, workloads.config_seed(CONFIG_NAME) + 7919 * rank)
+    in_bytes = x.nbytes
+    n, S = bank.nchan, bank.nspectra
+    plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window)
+    d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).to(dev)
+    acc = torch.zeros(plan.out_floats, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step_device():
+        plan.execute(d_in, S, acc, stream)
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step_device()
+    torch.cuda.synchronize()
+
+    gpu_index = local_rank
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local_rank])
+        except (ValueError, IndexError):
+            pass
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.2)
+
+    plan.set_profiling(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)            # L2 flush: 256 MiB written between steps
+        starts[i].record(stream)
+        step_device()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    stats = plan.kernel_stats()
+    plan.set_profiling(False)
+
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * S * n / (total_ms * 1e-3) / 1e9  # GHz, all ranks
+
+    # dominant kernel: live CUDA-event times from the timed region
+    peak, peak_kind = _peaks()
+    per_spec_bytes = n * bank.npol * 2 + 2.0 * n * 16 / S  # int8 input once + accumulator RMW per dump
+    dom = max(stats, key=lambda r: r[3])
+    name, launches, spectra, kms = dom
+    achieved = (spectra * per_spec_bytes) / (kms * 1e-3) / 1e9
+    spl = spectra / max(1, launches)
+    traffic = _traffic(name, spl)
+    path_bytes = args.steps * S * per_spec_bytes
+    kernels = {r[0]: {"launches": r[1], "total_ms": round(r[3], 4),
+                      "share": round(r[3] / max(1e-9, sum(q[3] for q in stats)), 4)} for r in stats}
+    gpu_launches = sum(r[1] for r in stats)
+
+    # end to end: pinned host input -> device, execute, dump to pinned host
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).pin_memory()
+        h_out = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
+        d_in2 = torch.empty_like(d_in)
+        e2e_steps = max(3, min(args.steps, 50))
+        for _ in range(2):
+            d_in2.copy_(h_in, non_blocking=True)
+            plan.execute(d_in2, S, acc, stream)
+            plan.dump(acc, h_out, stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            d_in2.copy_(h_in, non_blocking=True)
+            plan.execute(d_in2, S, acc, stream)
+            plan.dump(acc, h_out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * e2e_steps * S * n / (ems * 1e-3) / 1e9, "unit": "GHz",
+               "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(plan.out_floats * 4),
+               "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        ghz, s_used, dt = _oracle_rate(bank, x, 15.0, threads)
+        cpu = {"value": ghz, "unit": "GHz", "cores": threads, "kind": "oracle",
+               "sample": f"first {s_used} of {S} spectra of the same input, one run ({dt:.1f} s)"}
+
+    plan.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GHz", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nchan": n, "ntaps": bank.ntaps, "npol": bank.npol,
+                       "nspectra": S, "input_bytes": int(in_bytes),
+                       "l2": "flushed between steps (256 MiB write outside the timed interval)",
+                       "parallelism": f"replicas x{world} (independent beams)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                         "peak_source": peak_kind,
+                         "algorithmic_bytes_per_spectrum": per_spec_bytes},
+            "path_roofline": {"achieved": path_bytes / (total_ms * 1e-3) / 1e9 / world * world,
+                              "frac": path_bytes / (total_ms * 1e-3) / 1e9 / peak},
+            "kernels": kernels,
+            "gpu_launches": gpu_launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} | {"samples": clk["samples"]},
+            "complex_gsps": 2 * value,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * vspec.h — C ABI of the GB300 streaming channelizer (arXiv 1411.0436).
+ *
+ * The library implements the GPU spectrometer of §4 of "A GPU-Based Wide-Band
+ * Radio Spectrometer": 8-bit dual- or single-polarisation complex voltages
+ * are pre-filtered by a P-tap polyphase filter bank (or not, in direct-FFT
+ * mode, §5), transformed by an N-point FFT per polarisation, detected into
+ * X^2, Y^2, Re(XY*) and Im(XY*) and accumulated over the integration (§4).
+ * The initialisation steps of §4's algorithm (loading filter coefficients,
+ * creating the FFT plan) map to vspec_plan_create; the processing loop
+ * (pre-filter, FFTs, accumulate) maps to vspec_execute; copying the output to
+ * the host maps to vspec_dump.
+ *
+ * Conventions (the paper leaves these unstated; they are fixed here):
+ *   - input layout   int8, [time][pol][re, im]; single-pol is [time][re, im];
+ *   - coefficients   h[i] = w[i] * sinc((i - (L-1)/2) / N), L = P*N, with a
+ *                    symmetric window w of length L (rect, Hann or Hamming);
+ *                    direct mode multiplies by the bare window of length N;
+ *   - tap order      h[t*N + n] multiplies frame s+t of spectrum s;
+ *   - hop            N samples (critically sampled filter bank);
+ *   - DFT            X[k] = sum_n y[n] exp(-2 pi i n k / N), unnormalised,
+ *                    natural channel order (k = 0 is DC);
+ *   - output         npol == 2: float4 per channel (XX, YY, Re XY*, Im XY*),
+ *                    XY* = X * conj(Y); npol == 1: one float (XX) per channel;
+ *   - accumulation   a plain FP32 sum over spectra into the caller's buffer.
+ *
+ * All device pointers are plain CUDA device addresses (for example from
+ * cudaMalloc or a framework's allocator); `stream` is a cudaStream_t passed as
+ * void* (NULL selects the legacy default stream). No call throws; every call
+ * returns a vspec_status. Calls on one plan must not run concurrently from
+ * several host threads; separate plans are independent.
+ */
+#ifndef VSPEC_H
+#define VSPEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VSPEC_API __attribute__((visibility("default")))
+#else
+#define VSPEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VSPEC_OK = 0,
+    VSPEC_ERR_INVALID_ARG = -1,    /* a size, mode, window or pointer is out of range   */
+    VSPEC_ERR_UNSUPPORTED = -2,    /* a valid combination this build does not implement */
+    VSPEC_ERR_ALIGNMENT = -3,      /* a device pointer is not 16-byte aligned           */
+    VSPEC_ERR_CUDA = -4,           /* a CUDA runtime call or kernel launch failed       */
+    VSPEC_ERR_OOM = -5,            /* device memory for the plan could not be allocated */
+    VSPEC_ERR_DEVICE_TIMEOUT = -6  /* a bounded device-side wait expired                */
+} vspec_status;
+
+typedef enum { VSPEC_PFB = 0, VSPEC_DIRECT = 1 } vspec_mode;
+
+typedef enum { VSPEC_WIN_RECT = 0, VSPEC_WIN_HANN = 1, VSPEC_WIN_HAMMING = 2 } vspec_window;
+
+typedef struct vspec_plan vspec_plan;
+
+/*
+ * Create a plan (§4, initialisation: load the filter coefficients and create
+ * the FFT plan for the polarisations processed in parallel).
+ *   nchan   channels N: a power of two in [16, 2^20];
+ *   ntaps   taps P: 1..16 in PFB mode; 0 or 1 in direct mode;
+ *   npol    1 or 2;
+ *   mode    VSPEC_PFB or VSPEC_DIRECT;
+ *   window  VSPEC_WIN_RECT, VSPEC_WIN_HANN or VSPEC_WIN_HAMMING.
+ * Coefficients and twiddle factors are generated on the current CUDA device in
+ * FP64 and stored in FP32; the plan also owns its scratch buffers. The plan is
+ * bound to the device that is current at creation. On success *out holds the
+ * plan; on failure *out is set to NULL and nothing is leaked.
+ * Errors: VSPEC_ERR_INVALID_ARG (bad argument or out == NULL),
+ * VSPEC_ERR_UNSUPPORTED (a PFB with nchan above the sizes this build's
+ * kernels hold on chip), VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
+                               vspec_mode mode, vspec_window window);
+
+/* Release a plan and all device memory it owns. NULL is accepted. The caller
+ * must make sure no work using the plan is still running on any stream. */
+VSPEC_API vspec_status vspec_plan_destroy(vspec_plan *plan);
+
+/*
+ * Channelize nspectra spectra and add them to d_accum (§4, processing loop:
+ * pre-filter, parallel FFTs, accumulate).
+ *   d_in     device int8 [(nspectra + P_eff - 1) * nchan][npol][2], P_eff = ntaps
+ *            in PFB mode and 1 in direct mode; spectrum s uses samples
+ *            [s*nchan, (s + P_eff)*nchan). A streaming caller overlaps
+ *            consecutive calls' inputs by (P_eff - 1) * nchan samples.
+ *   nspectra number of spectra, >= 0 (0 is a no-op).
+ *   d_accum  device float[nchan * 4] (npol == 2, float4 per channel) or
+ *            float[nchan] (npol == 1); accumulated into, never cleared here.
+ *   stream   cudaStream_t (as void*) on which all work is enqueued.
+ * Both pointers must be 16-byte aligned. The call is asynchronous: it returns
+ * once the work is enqueued; the caller owns d_in and d_accum and must keep
+ * them alive until the stream reaches the end of this call's work.
+ * Errors: VSPEC_ERR_INVALID_ARG (NULL plan/pointer, nspectra < 0),
+ * VSPEC_ERR_ALIGNMENT, VSPEC_ERR_CUDA (launch failure; the plan stays usable).
+ */
+VSPEC_API vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra,
+                           float *d_accum, void *stream);
+
+/*
+ * Dump the accumulator (§4, "copy output to host") and clear it.
+ *   h_out  host buffer of nchan * (npol == 2 ? 4 : 1) floats, or NULL to clear
+ *          only. Pinned host memory makes the copy asynchronous; with pageable
+ *          memory the copy completes before the call returns.
+ * Enqueues on `stream`: a device-to-host copy of d_accum into h_out (if not
+ * NULL), then a clear of d_accum to zero. The caller synchronises the stream
+ * before reading h_out.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_ALIGNMENT, VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *stream);
+
+/*
+ * Plan properties: bytes of device scratch the plan owns (coefficients,
+ * twiddles and intermediate buffers) and the number of passes the design makes
+ * over the int8 input in HBM per execute (1: every input byte is fetched from
+ * HBM once; overlapping PFB frames are re-read from on-chip storage or L2).
+ * Either output pointer may be NULL.
+ */
+VSPEC_API vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int *hbm_passes);
+
+/*
+ * Instrumentation. With profiling enabled, vspec_execute records a pair of
+ * CUDA events on its stream around every kernel it launches; with it
+ * disabled (the default) no event is recorded. Enabling or disabling clears
+ * the records.
+ */
+VSPEC_API vspec_status vspec_plan_set_profiling(vspec_plan *plan, int enable);
+
+/*
+ * Per-kernel totals of the records made since profiling was enabled (or
+ * since the last read with reset != 0): for kernel kind `kind` (0-based; a
+ * kind past the last returns VSPEC_ERR_INVALID_ARG), its name, the number
+ * of launches, the spectra those launches processed and the summed
+ * event-measured duration in milliseconds. Reading waits for the recorded
+ * events to complete. Any output pointer may be NULL.
+ */
+VSPEC_API vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset,
+                                               const char **name, long long *launches,
+                                               long long *spectra, double *total_ms);
+
+/* Static, human-readable text for a status code. */
+VSPEC_API const char *vspec_status_string(vspec_status status);
+
+/* Text of the most recent CUDA error seen by this library in the calling
+ * thread ("" if none). The pointer stays valid until the thread's next call. */
+VSPEC_API const char *vspec_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSPEC_H */

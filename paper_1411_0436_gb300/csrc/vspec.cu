@@ -1,0 +1,508 @@
+// vspec.cu — host side of the C ABI declared in include/vspec.h.
+//
+// Plan creation follows the initialisation steps of §4 of arXiv 1411.0436
+// (load the filter coefficients, create the FFT plan); execution follows its
+// processing loop (pre-filter, FFTs, accumulate) and the dump its final copy
+// to the host. The device code is in vspec_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vspec.h"
+#include "vspec_kernels.cuh"
+
+using vspec::Pass;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vspec_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return VSPEC_ERR_CUDA;
+}
+
+#define VSPEC_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+    int e = 0;
+    while ((1LL << e) < v) e++;
+    return e;
+}
+
+// Radices of a length-2^e DFT: passes of at most maxbits bits, as even as
+// possible.
+std::vector<int> radix_list(int e, int maxbits = 4) {
+    std::vector<int> r;
+    if (e == 0) return r;
+    const int np = (e + maxbits - 1) / maxbits;
+    for (int i = 0; i < np; i++) {
+        const int bits = e / np + (i < e % np ? 1 : 0);
+        r.push_back(1 << bits);
+    }
+    return r;
+}
+
+// DIF pass descriptors and twiddle-table offsets for a length-L transform.
+std::vector<Pass> make_passes(int L, const std::vector<int> &radices, int *tw_entries) {
+    std::vector<Pass> ps;
+    int lb = L, off = 0;
+    for (int r : radices) {
+        Pass p;
+        p.r = r;
+        p.lb = lb;
+        p.m = lb / r;
+        p.off = off;
+        off += p.m * (r - 1);
+        ps.push_back(p);
+        lb /= r;
+    }
+    *tw_entries = off;
+    return ps;
+}
+
+// Output index held by in-place position pos after the DIF passes:
+// pos = sum_i q_i * M_i  ->  k = q_1 + r_1 (q_2 + r_2 (...)).
+std::vector<int> digit_reverse(int L, const std::vector<int> &radices) {
+    std::vector<int> k_of_pos(L);
+    for (int pos = 0; pos < L; pos++) {
+        int rem = pos, lb = L, k = 0, scale = 1;
+        for (int r : radices) {
+            const int m = lb / r;
+            const int q = rem / m;
+            rem -= q * m;
+            k += q * scale;
+            scale *= r;
+            lb = m;
+        }
+        k_of_pos[pos] = k;
+    }
+    return k_of_pos;
+}
+
+}  // namespace
+
+struct vspec_plan {
+    int N = 0, P = 0, npol = 0, mode = 0, window = 0, device = 0;
+    int N1 = 0, N2 = 0, C = 0, PT = 0, PPT = 0, TA = 0, RB = 0, TB = 0;
+    int num_sms = 0, occA = 1, occB = 1;
+    int sc_max = 1, groups_b = 1;
+    size_t smemA = 0, smemB = 0;
+    std::vector<Pass> passA, passB;
+    float *coef = nullptr;
+    float2 *twA = nullptr, *twB = nullptr, *twZ = nullptr;
+    int *invA = nullptr, *invB = nullptr;
+    void *Z = nullptr, *partial = nullptr;
+    size_t scratch_bytes = 0;
+    const void *kernelA = nullptr, *kernelB = nullptr, *kernelR = nullptr;
+    // instrumentation (vspec_plan_set_profiling)
+    struct Rec {
+        int kind;
+        int spectra;
+        cudaEvent_t start, stop;
+    };
+    bool profiling = false;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
+    using namespace vspec;
+    if (PT == 1 && PPT == 1) return (const void *)fir_colfft_kernel<NPOL, 1, 1>;
+    if (PT == 1 && PPT == 2) return (const void *)fir_colfft_kernel<NPOL, 1, 2>;
+    if (PT == 1 && PPT == 4) return (const void *)fir_colfft_kernel<NPOL, 1, 4>;
+    if (PT == 1 && PPT == 8) return (const void *)fir_colfft_kernel<NPOL, 1, 8>;
+    if (PT == 2 && PPT == 1) return (const void *)fir_colfft_kernel<NPOL, 2, 1>;
+    if (PT == 2 && PPT == 2) return (const void *)fir_colfft_kernel<NPOL, 2, 2>;
+    if (PT == 4 && PPT == 1) return (const void *)fir_colfft_kernel<NPOL, 4, 1>;
+    if (PT == 4 && PPT == 2) return (const void *)fir_colfft_kernel<NPOL, 4, 2>;
+    if (PT == 8 && PPT == 1) return (const void *)fir_colfft_kernel<NPOL, 8, 1>;
+    if (PT == 8 && PPT == 2) return (const void *)fir_colfft_kernel<NPOL, 8, 2>;
+    if (PT == 16 && PPT == 1) return (const void *)fir_colfft_kernel<NPOL, 16, 1>;
+    return nullptr;
+}
+
+constexpr int kNumKinds = 3;
+const char *const kKindNames[kNumKinds] = {"fir_colfft", "rowfft_detect", "reduce"};
+
+void release_records(vspec_plan *p) {
+    for (auto &r : p->recs) {
+        p->event_pool.push_back(r.start);
+        p->event_pool.push_back(r.stop);
+    }
+    p->recs.clear();
+}
+
+cudaError_t take_event(vspec_plan *p, cudaEvent_t *ev) {
+    if (!p->event_pool.empty()) {
+        *ev = p->event_pool.back();
+        p->event_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(ev);
+}
+
+// Launch one kernel on st; in profiling mode bracket it with events.
+vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 grid, dim3 block,
+                    void **args, size_t smem, cudaStream_t st) {
+    vspec_plan::Rec r{kind, spectra, nullptr, nullptr};
+    if (p->profiling) {
+        VSPEC_CUDA(take_event(p, &r.start));
+        VSPEC_CUDA(take_event(p, &r.stop));
+        VSPEC_CUDA(cudaEventRecord(r.start, st));
+    }
+    cudaError_t e = cudaLaunchKernel(fn, grid, block, args, smem, st);
+    if (e != cudaSuccess) {
+        if (p->profiling) {
+            p->event_pool.push_back(r.start);
+            p->event_pool.push_back(r.stop);
+        }
+        return cuda_fail(e, kKindNames[kind]);
+    }
+    if (p->profiling) {
+        VSPEC_CUDA(cudaEventRecord(r.stop, st));
+        p->recs.push_back(r);
+    }
+    return VSPEC_OK;
+}
+
+void free_plan(vspec_plan *p) {
+    if (!p) return;
+    release_records(p);
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    cudaFree(p->coef);
+    cudaFree(p->twA);
+    cudaFree(p->twB);
+    cudaFree(p->twZ);
+    cudaFree(p->invA);
+    cudaFree(p->invB);
+    cudaFree(p->Z);
+    cudaFree(p->partial);
+    delete p;
+}
+
+vspec_status dev_alloc(void **ptr, size_t bytes, size_t *total) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        g_last_error = "cudaMalloc: out of memory";
+        return VSPEC_ERR_OOM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    *total += bytes;
+    return VSPEC_OK;
+}
+
+// Chunk scratch budget: the per-chunk intermediate stays resident in L2.
+constexpr size_t kScratchBudget = 32u << 20;
+constexpr int kRowElems = 2048;  // target row-DFT elements per kernel-B CTA
+
+vspec_status build_plan(vspec_plan *p) {
+    const int N = p->N;
+    const int e = ilog2(N);
+    const bool pfb = p->mode == VSPEC_PFB;
+    const int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
+    const int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
+    // largest column length kernel A can hold in registers (512 threads)
+    int n2max;
+    if (!pfb) n2max = 4096 / cmin;
+    else if (PT <= 8) n2max = 1024 / cmin;
+    else n2max = 512 / cmin;
+    // smallest N2 that brings N1 to at most 2048 (4096 if the columns are full)
+    int N2 = 1;
+    while (N / N2 > kRowElems && N2 < n2max) N2 *= 2;
+    const int N1 = N / N2;
+    if (N1 > 4096) {
+        g_last_error = "nchan too large for this mode in this build";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    int C = std::max(cmin, 256 / N2);
+    C = std::min(C, N1);
+    const int pts = N2 * C;
+    const int TA = std::min(512, pts);
+    const int PPT = pts / TA;
+    p->N1 = N1;
+    p->N2 = N2;
+    p->C = C;
+    p->PT = PT;
+    p->PPT = PPT;
+    p->TA = TA;
+    p->kernelA = p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT);
+    if (!p->kernelA) {
+        g_last_error = "no kernel instance for this tap count and size";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    p->kernelB = p->npol == 2 ? (const void *)vspec::rowfft_detect_kernel<2>
+                              : (const void *)vspec::rowfft_detect_kernel<1>;
+    p->kernelR = p->npol == 2 ? (const void *)vspec::reduce_kernel<2> : (const void *)vspec::reduce_kernel<1>;
+
+    const int e2 = ilog2(N2), e1 = e - e2;
+    // Kernel A keeps its register window live through the column DFTs: cap
+    // the butterfly width so both fit in 128 registers.
+    const int capA = vspec::col_radix_cap(p->npol, PT, PPT);
+    const int maxbitsA = capA == 16 ? 4 : capA == 8 ? 3 : 2;
+    const std::vector<int> rA = radix_list(e2, maxbitsA), rB = radix_list(e1);
+    int twA_n = 0, twB_n = 0;
+    p->passA = make_passes(N2, rA, &twA_n);
+    p->passB = make_passes(N1, rB, &twB_n);
+    if ((int)p->passA.size() > vspec::kMaxPasses || (int)p->passB.size() > vspec::kMaxPasses ||
+        p->passB.empty()) {
+        g_last_error = "pass count out of range";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    p->RB = std::max(1, std::min(N2, kRowElems / N1));
+    int maxb = 1;
+    for (const Pass &ps : p->passB) maxb = std::max(maxb, p->RB * (N1 / ps.r));
+    p->TB = std::min(256, std::max(32, maxb));
+
+    const size_t elem = p->npol == 2 ? sizeof(float4) : sizeof(float2);
+    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+    p->smemA = (size_t)PT * N2 * C * elem;
+    p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
+
+    VSPEC_CUDA(cudaGetDevice(&p->device));
+    VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
+    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occA, p->kernelA, p->TA, p->smemA));
+    VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occB, p->kernelB, p->TB, p->smemB));
+    if (p->occA < 1 || p->occB < 1) {
+        g_last_error = "kernel does not fit on an SM";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+
+    p->sc_max = (int)std::max<size_t>(1, kScratchBudget / ((size_t)N * elem));
+    const int blocksB = N2 / p->RB;
+    const int targetB = p->num_sms * p->occB;
+    p->groups_b = std::max(1, std::min(p->sc_max, (targetB + blocksB - 1) / blocksB));
+
+    // device tables and scratch
+    vspec_status st;
+    size_t tot = 0;
+    const int Lc = (pfb ? p->P : 1) * N;
+    if ((st = dev_alloc((void **)&p->coef, sizeof(float) * (size_t)Lc, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twA, sizeof(float2) * (size_t)std::max(1, twA_n), &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twB, sizeof(float2) * (size_t)std::max(1, twB_n), &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twZ, sizeof(float2) * (size_t)N, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->invA, sizeof(int) * (size_t)N2, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
+    if ((st = dev_alloc(&p->Z, (size_t)p->sc_max * N * elem, &tot))) return st;
+    if ((st = dev_alloc(&p->partial, (size_t)p->groups_b * N * accel, &tot))) return st;
+    p->scratch_bytes = tot;
+
+    // digit-reversal maps (host) -> inverse maps for the final scatter
+    const std::vector<int> kA = digit_reverse(N2, rA), kB = digit_reverse(N1, rB);
+    std::vector<int> invA(N2), invB(N1);
+    for (int pos = 0; pos < N2; pos++) invA[kA[pos]] = pos;
+    for (int pos = 0; pos < N1; pos++) invB[kB[pos]] = pos;
+    int *d_kA = nullptr;
+    if ((st = dev_alloc((void **)&d_kA, sizeof(int) * N2, &tot))) return st;
+    p->scratch_bytes = tot - sizeof(int) * N2;
+    cudaStream_t s0 = nullptr;
+    cudaError_t ce = cudaMemcpy(d_kA, kA.data(), sizeof(int) * N2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->invA, invA.data(), sizeof(int) * N2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->invB, invB.data(), sizeof(int) * N1, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        vspec::gen_coef_kernel<<<(Lc + 255) / 256, 256, 0, s0>>>(p->coef, N, Lc, pfb ? 1 : 0, p->window);
+        for (const Pass &ps : p->passA)
+            if (ps.m * (ps.r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256, 0, s0>>>(p->twA, ps);
+        for (const Pass &ps : p->passB)
+            if (ps.m * (ps.r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256, 0, s0>>>(p->twB, ps);
+        vspec::gen_twz_kernel<<<(N + 255) / 256, 256, 0, s0>>>(p->twZ, N, N1, N2, d_kA);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    }
+    cudaFree(d_kA);
+    if (ce != cudaSuccess) return cuda_fail(ce, "plan tables");
+    return VSPEC_OK;
+}
+
+bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *vspec_status_string(vspec_status s) {
+    switch (s) {
+        case VSPEC_OK: return "ok";
+        case VSPEC_ERR_INVALID_ARG: return "invalid argument";
+        case VSPEC_ERR_UNSUPPORTED: return "unsupported configuration";
+        case VSPEC_ERR_ALIGNMENT: return "pointer not 16-byte aligned";
+        case VSPEC_ERR_CUDA: return "CUDA error";
+        case VSPEC_ERR_OOM: return "out of device memory";
+        case VSPEC_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *vspec_last_error(void) { return g_last_error.c_str(); }
+
+vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
+                               vspec_window window) {
+    if (!out) return VSPEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!is_pow2(nchan) || nchan < 16 || nchan > (1 << 20)) return VSPEC_ERR_INVALID_ARG;
+    if (npol != 1 && npol != 2) return VSPEC_ERR_INVALID_ARG;
+    if (mode != VSPEC_PFB && mode != VSPEC_DIRECT) return VSPEC_ERR_INVALID_ARG;
+    if (window != VSPEC_WIN_RECT && window != VSPEC_WIN_HANN && window != VSPEC_WIN_HAMMING)
+        return VSPEC_ERR_INVALID_ARG;
+    if (mode == VSPEC_PFB && (ntaps < 1 || ntaps > 16)) return VSPEC_ERR_INVALID_ARG;
+    if (mode == VSPEC_DIRECT && (ntaps < 0 || ntaps > 1)) return VSPEC_ERR_INVALID_ARG;
+
+    vspec_plan *p = new (std::nothrow) vspec_plan();
+    if (!p) return VSPEC_ERR_OOM;
+    p->N = nchan;
+    p->P = mode == VSPEC_PFB ? ntaps : 1;
+    p->npol = npol;
+    p->mode = mode;
+    p->window = window;
+    vspec_status st = build_plan(p);
+    if (st != VSPEC_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_destroy(vspec_plan *plan) {
+    free_plan(plan);
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int *hbm_passes) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (scratch_bytes) *scratch_bytes = plan->scratch_bytes;
+    if (hbm_passes) *hbm_passes = 1;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
+                           void *stream) {
+    if (!plan || !d_in || !d_accum || nspectra < 0) return VSPEC_ERR_INVALID_ARG;
+    if (!aligned16(d_in) || !aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
+    if (nspectra == 0) return VSPEC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    vspec_plan *p = plan;
+    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+
+    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->groups_b * p->N * accel, st));
+
+    const int sc_full = std::min(nspectra, p->sc_max);
+    const int blocksA = p->N1 / p->C;
+    const int targetA = p->num_sms * p->occA;
+
+    vspec::ColParams ca;
+    ca.in = d_in;
+    ca.coef = p->coef;
+    ca.twA = p->twA;
+    ca.twZ = p->twZ;
+    ca.Z = p->Z;
+    ca.N = p->N;
+    ca.N1 = p->N1;
+    ca.N2 = p->N2;
+    ca.C = p->C;
+    ca.P = p->P;
+    ca.npass = (int)p->passA.size();
+    for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
+
+    vspec::RowParams cb;
+    cb.Z = p->Z;
+    cb.partial = p->partial;
+    cb.twB = p->twB;
+    cb.N = p->N;
+    cb.N1 = p->N1;
+    cb.N2 = p->N2;
+    cb.RB = p->RB;
+    cb.npass = (int)p->passB.size();
+    for (int i = 0; i < cb.npass; i++) cb.pass[i] = p->passB[i];
+    cb.groups = p->groups_b;
+
+    for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
+        const int sc = std::min(sc_full, nspectra - s0);
+        int ga = (targetA + blocksA - 1) / blocksA;
+        ga = std::max(1, std::min(ga, sc));
+        ca.s0 = s0;
+        ca.sc = sc;
+        ca.groups = ga;
+        void *argsA[] = {&ca};
+        vspec_status r = launch(p, 0, sc, p->kernelA, dim3(blocksA, ga), dim3(p->TA), argsA, p->smemA, st);
+        if (r != VSPEC_OK) return r;
+        cb.sc = sc;
+        void *argsB[] = {&cb};
+        r = launch(p, 1, sc, p->kernelB, dim3(p->N2 / p->RB, p->groups_b), dim3(p->TB), argsB, p->smemB, st);
+        if (r != VSPEC_OK) return r;
+    }
+    {
+        const void *part = p->partial;
+        int groups = p->groups_b, N = p->N, N1 = p->N1, N2 = p->N2;
+        const int *ia = p->invA, *ib = p->invB;
+        void *outp = d_accum;
+        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
+        vspec_status r = launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+        if (r != VSPEC_OK) return r;
+    }
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_set_profiling(vspec_plan *plan, int enable) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    for (auto &r : plan->recs) cudaEventSynchronize(r.stop);
+    release_records(plan);
+    plan->profiling = enable != 0;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset, const char **name,
+                                     long long *launches, long long *spectra, double *total_ms) {
+    if (!plan || kind < 0 || kind >= kNumKinds) return VSPEC_ERR_INVALID_ARG;
+    long long n = 0, sp = 0;
+    double ms = 0.0;
+    for (auto &r : plan->recs) {
+        if (r.kind != kind) continue;
+        VSPEC_CUDA(cudaEventSynchronize(r.stop));
+        float t = 0.f;
+        VSPEC_CUDA(cudaEventElapsedTime(&t, r.start, r.stop));
+        ms += t;
+        n++;
+        sp += r.spectra;
+    }
+    if (name) *name = kKindNames[kind];
+    if (launches) *launches = n;
+    if (spectra) *spectra = sp;
+    if (total_ms) *total_ms = ms;
+    if (reset) {
+        for (auto &r : plan->recs) cudaEventSynchronize(r.stop);
+        release_records(plan);
+    }
+    return VSPEC_OK;
+}
+
+vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *stream) {
+    if (!plan || !d_accum) return VSPEC_ERR_INVALID_ARG;
+    if (!aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)plan->N * (plan->npol == 2 ? 4 : 1) * sizeof(float);
+    if (h_out) VSPEC_CUDA(cudaMemcpyAsync(h_out, d_accum, bytes, cudaMemcpyDeviceToHost, st));
+    VSPEC_CUDA(cudaMemsetAsync(d_accum, 0, bytes, st));
+    return VSPEC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,431 @@
+// vspec_kernels.cuh — device code of the channelizer (§4 of arXiv 1411.0436).
+//
+// The N-point DFT of every spectrum is split as N = N1 * N2 (four-step):
+//   n = n1 + N1*n2,  k = k2 + N2*k1,
+//   X[k2 + N2 k1] = sum_n1 W_N1^(n1 k1) [ W_N^(n1 k2) sum_n2 y[n1 + N1 n2] W_N2^(n2 k2) ].
+// Kernel A (fir_colfft) owns a block of C consecutive columns n1 and all N2
+// rows across a run of spectra. Each thread keeps the last P frames of its
+// samples in registers as fp32, so every input byte is read from memory once
+// per run. It applies the pre-filter (§4, PFB), runs the column DFTs over n2
+// in shared memory, multiplies by W_N^(n1 k2) and writes the chunk scratch Z
+// (sized to stay in L2). Kernel B (rowfft_detect) owns rows k2 and runs the
+// row DFTs over n1, fused with detection (§4: X^2, Y^2, Re XY*, Im XY*) and
+// accumulation in shared memory (§4, accumulate). A last small kernel adds
+// the per-group partial sums into the caller's accumulator in channel order.
+//
+// Both kernels use in-place decimation-in-frequency passes: a pass of radix r
+// over blocks of length lb reads v[q] = x[j + q*m] (m = lb / r), computes the
+// r-point DFT, multiplies output q by W_lb^(j*q) and writes it back to
+// x[j + q*m]. After all passes, position sum_i q_i * M_i holds output index
+// q_1 + r_1 (q_2 + r_2 (q_3 + ...)); the plan precomputes those
+// digit-reversal maps and only the final scatter into channel order uses them.
+#pragma once
+#include <cstdint>
+#include <utility>
+
+#include "vspec_radix.cuh"
+
+namespace vspec {
+
+constexpr int kMaxPasses = 6;
+
+template <int NPOL> struct Elem;
+template <> struct Elem<1> {
+    using T = float2;     // one complex sample
+    using Acc = float;    // XX
+};
+template <> struct Elem<2> {
+    using T = float4;     // both polarisations of one sample or channel
+    using Acc = float4;   // XX, YY, Re XY*, Im XY*
+};
+
+struct ColParams {
+    const int8_t *in;    // sample m of pol p at in[(m * npol + p) * 2 + {0: re, 1: im}]
+    const float *coef;   // pre-filter coefficients h[t * N + n], t < P (fp32)
+    const float2 *twA;   // per-pass twiddles of the length-N2 column DFTs
+    const float2 *twZ;   // [pos][n1]: W_N^(n1 * k2(pos)) (rows in pass-output order)
+    void *Z;             // chunk scratch [s_local][pos][n1] of Elem::T
+    int N, N1, N2, C, P, npass;
+    Pass pass[kMaxPasses];
+    long long s0;        // absolute index of the chunk's first spectrum
+    int sc;              // spectra in this chunk
+    int groups;          // spectrum groups per chunk (gridDim.y)
+};
+
+struct RowParams {
+    const void *Z;       // chunk scratch written by kernel A
+    void *partial;       // [group][pos][posB] of Elem::Acc, accumulated into
+    const float2 *twB;   // per-pass twiddles of the length-N1 row DFTs
+    int N, N1, N2, RB, npass;
+    Pass pass[kMaxPasses];
+    int sc, groups;
+};
+
+// ---------------------------------------------------------------- unpack ---
+// Exact int8 -> fp32: placing (b ^ 0x80) in the low mantissa byte of 2^23
+// gives the float 2^23 + b + 128; subtracting 2^23 + 128 leaves b exactly.
+__device__ __forceinline__ float unpack_byte(uint32_t wx, int i) {
+    return __int_as_float(__byte_perm(wx, 0x4B000000u, 0x7540u + i)) - 8388736.0f;
+}
+
+template <int NPOL> __device__ __forceinline__ uint32_t load_raw(const int8_t *in, long long m);
+template <> __device__ __forceinline__ uint32_t load_raw<2>(const int8_t *in, long long m) {
+    return __ldg(reinterpret_cast<const unsigned int *>(in) + m);
+}
+template <> __device__ __forceinline__ uint32_t load_raw<1>(const int8_t *in, long long m) {
+    return (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(in) + m);
+}
+
+// ------------------------------------------------------ kernel A helpers ---
+
+template <int R, int NPOL>
+__device__ __forceinline__ void col_butterfly(const ColParams &p, typename Elem<NPOL>::T *data,
+                                              typename Elem<NPOL>::T *Zs, const Pass ps,
+                                              bool last, int c, int b, int j, int n1) {
+    using T = typename Elem<NPOL>::T;
+    const int C = p.C;
+    const int base = b * ps.lb + j;
+    T v[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) v[q] = data[(base + q * ps.m) * C + c];
+    Dft<R>::run(v);
+    if (!last) {
+        if (ps.m > 1) {
+            const float2 *tw = p.twA + ps.off + j * (R - 1);
+#pragma unroll
+            for (int q = 1; q < R; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) data[(base + q * ps.m) * C + c] = v[q];
+    } else {
+        // last pass: m == 1, outputs at positions base + q
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const size_t zi = (size_t)(base + q) * p.N1 + n1;
+            Zs[zi] = cmul(v[q], __ldg(p.twZ + zi));
+        }
+    }
+}
+
+// Column DFTs of a batch of nb spectra (data holds their pre-filter outputs,
+// [spectrum][n2][c]), then W_N^(n1 k2) and the store into the chunk scratch.
+template <int NPOL, int RMAX>
+__device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<NPOL>::T *data,
+                                              int s_local0, int nb) {
+    using T = typename Elem<NPOL>::T;
+    const int C = p.C, N2 = p.N2;
+    const int pts = N2 * C;
+    const int n1_0 = blockIdx.x * C;
+    if (p.npass == 0) {  // N2 == 1: the pre-filter output is the row itself
+        for (int u = threadIdx.x; u < nb * C; u += blockDim.x) {
+            const int sb = u / C, c = u - sb * C;
+            T *Zs = reinterpret_cast<T *>(p.Z) + (size_t)(s_local0 + sb) * p.N;
+            Zs[n1_0 + c] = data[u];
+        }
+    }
+    for (int ip = 0; ip < p.npass; ip++) {
+        const Pass ps = p.pass[ip];
+        const bool last = ip == p.npass - 1;
+        const int per = C * (N2 / ps.r);  // butterflies per spectrum
+        for (int u = threadIdx.x; u < nb * per; u += blockDim.x) {
+            const int sb = u / per, w = u - sb * per;
+            const int c = w & (C - 1), bj = w / C;
+            const int b = bj / ps.m, j = bj - b * ps.m;
+            T *d = data + sb * pts;
+            T *Zs = reinterpret_cast<T *>(p.Z) + (size_t)(s_local0 + sb) * p.N;
+            if (ps.r == 2) col_butterfly<2, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
+            else if (ps.r == 4 || RMAX < 8) col_butterfly<4, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
+            else if (ps.r == 8 || RMAX < 16) col_butterfly<(RMAX < 8 ? 4 : 8), NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
+            else col_butterfly<RMAX, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
+        }
+        __syncthreads();
+    }
+    if (p.npass == 0) __syncthreads();
+}
+
+// Widest column butterfly kernel A may use next to its register window.
+// Window registers per thread are ppt * pt * (2 npol + 1); an r-point
+// butterfly holds r * 2 npol more floats.
+__host__ __device__ constexpr int col_radix_cap(int npol, int pt, int ppt) {
+    return ppt * pt * (2 * npol + 1) + 16 * 2 * npol <= 72 ? 16
+         : ppt * pt * (2 * npol + 1) + 8 * 2 * npol <= 72 ? 8 : 4;
+}
+
+// ---------------------------------------------------------------- kernel A --
+// PT: taps held in the register window (P rounded up; the leading PT - P taps
+// have zero coefficients and read a clamped frame). PPT: samples per thread.
+// Spectra are processed in batches of PT: the window rotates once per batch,
+// so every slot index is a compile-time constant, and the batch's column
+// DFTs then run together. The window stays live through the column DFTs, so
+// the widest butterfly is capped by the window's register footprint; the
+// plan builds its pass list with the same cap (col_radix_cap).
+template <int NPOL, int PT, int PPT>
+__global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__ ColParams p) {
+    using T = typename Elem<NPOL>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
+    constexpr int NC = 2 * NPOL;  // floats per sample
+
+    const int g = blockIdx.y;
+    const int s_beg = (int)((long long)p.sc * g / p.groups);
+    const int s_end = (int)((long long)p.sc * (g + 1) / p.groups);
+    if (s_beg >= s_end) return;
+
+    const int C = p.C;
+    const int pts = p.N2 * C;
+    const int n1_0 = blockIdx.x * C;
+    const int D = PT - p.P;  // leading zero taps
+
+    long long n_pt[PPT];
+    int sm_pt[PPT];
+    float cf[PPT][PT];
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        const int idx = threadIdx.x + i * blockDim.x;  // = n2 * C + c
+        const int c = idx & (C - 1), n2 = idx / C;
+        n_pt[i] = n1_0 + c + (long long)p.N1 * n2;
+        sm_pt[i] = idx;
+#pragma unroll
+        for (int t = 0; t < PT; t++)
+            cf[i][t] = (t >= D) ? __ldg(p.coef + (size_t)(t - D) * p.N + n_pt[i]) : 0.0f;
+    }
+
+    // Slot (s - s_beg + t) % PT of the window holds frame s + t - D.
+    float win[PPT][PT][NC];
+    const long long sabs = p.s0 + s_beg;
+#pragma unroll
+    for (int t = 0; t < PT - 1; t++) {
+        long long f = sabs - D + t;
+        if (f < 0) f = 0;
+#pragma unroll
+        for (int i = 0; i < PPT; i++) {
+            const uint32_t wx = load_raw<NPOL>(p.in, f * p.N + n_pt[i]) ^ 0x80808080u;
+#pragma unroll
+            for (int k = 0; k < NC; k++) win[i][t][k] = unpack_byte(wx, k);
+        }
+    }
+
+    for (int s_base = s_beg; s_base < s_end; s_base += PT) {
+        const int nb = min(PT, s_end - s_base);
+#pragma unroll
+        for (int u = 0; u < PT; u++) {
+            if (u < nb) {
+                const long long fnew = p.s0 + s_base + u + p.P - 1;  // newest frame of spectrum s_base + u
+                const int snew = (u + PT - 1) % PT;
+#pragma unroll
+                for (int i = 0; i < PPT; i++) {
+                    const uint32_t wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]) ^ 0x80808080u;
+#pragma unroll
+                    for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
+                    float y[NC];
+#pragma unroll
+                    for (int k = 0; k < NC; k++) y[k] = cf[i][0] * win[i][u % PT][k];
+#pragma unroll
+                    for (int t = 1; t < PT; t++) {
+#pragma unroll
+                        for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
+                    }
+                    T *d = data + u * pts + sm_pt[i];
+                    if constexpr (NPOL == 2) *d = make_float4(y[0], y[1], y[2], y[3]);
+                    else *d = make_float2(y[0], y[1]);
+                }
+            }
+        }
+        __syncthreads();
+        col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, s_base, nb);
+    }
+}
+
+// ---------------------------------------------------------------- kernel B --
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+template <int NPOL> __device__ __forceinline__ void acc_add(float4 &a, float4 v) {
+    // detection of one channel of both polarisations (§4)
+    const float xx = fmaf(v.x, v.x, v.y * v.y);
+    const float yy = fmaf(v.z, v.z, v.w * v.w);
+    const float re = fmaf(v.x, v.z, v.y * v.w);   // Re(X conj Y)
+    const float im = fmaf(v.y, v.z, -v.x * v.w);  // Im(X conj Y)
+    a.x += xx;
+    a.y += yy;
+    a.z += re;
+    a.w += im;
+}
+__device__ __forceinline__ void acc_add1(float &a, float2 v) { a += fmaf(v.x, v.x, v.y * v.y); }
+
+template <int R, int NPOL>
+__device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<NPOL>::T *data,
+                                              typename Elem<NPOL>::Acc *acc,
+                                              const typename Elem<NPOL>::T *Zs, const Pass ps,
+                                              bool first, bool last, int r, int b, int j,
+                                              int rowstride) {
+    using T = typename Elem<NPOL>::T;
+    const int base = b * ps.lb + j;
+    T *row = data + r * rowstride;
+    T v[R];
+    if (first) {
+        const T *zr = Zs + (size_t)(blockIdx.x * p.RB + r) * p.N1;
+#pragma unroll
+        for (int q = 0; q < R; q++) v[q] = zr[base + q * ps.m];
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; q++) v[q] = row[pad16(base + q * ps.m)];
+    }
+    Dft<R>::run(v);
+    if (!last) {
+        if (ps.m > 1) {
+            const float2 *tw = p.twB + ps.off + j * (R - 1);
+#pragma unroll
+            for (int q = 1; q < R; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) row[pad16(base + q * ps.m)] = v[q];
+    } else {
+        // m == 1: output q of unit (r, b); accumulator slot q * U + (r * N1/R + b)
+        const int U = p.RB * (p.N1 / R);
+        const int w = r * (p.N1 / R) + b;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            if constexpr (NPOL == 2) acc_add<2>(acc[q * U + w], v[q]);
+            else acc_add1(acc[q * U + w], v[q]);
+        }
+    }
+}
+
+template <int NPOL>
+__global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_constant__ RowParams p) {
+    using T = typename Elem<NPOL>::T;
+    using A = typename Elem<NPOL>::Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rowstride = p.N1 + (p.N1 >> 4);
+    T *data = reinterpret_cast<T *>(smem_raw);
+    A *acc = reinterpret_cast<A *>(data + p.RB * rowstride);
+
+    const int g = blockIdx.y;
+    const int s_beg = (int)((long long)p.sc * g / p.groups);
+    const int s_end = (int)((long long)p.sc * (g + 1) / p.groups);
+    if (s_beg >= s_end) return;
+
+    const int nacc = p.RB * p.N1;
+    for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+        if constexpr (NPOL == 2) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else acc[e] = 0.f;
+    }
+    __syncthreads();
+
+    for (int s = s_beg; s < s_end; s++) {
+        const T *Zs = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
+        for (int ip = 0; ip < p.npass; ip++) {
+            const Pass ps = p.pass[ip];
+            const bool first = ip == 0, last = ip == p.npass - 1;
+            const int per_row = p.N1 / ps.r;
+            const int nb = p.RB * per_row;
+            for (int u = threadIdx.x; u < nb; u += blockDim.x) {
+                const int r = u / per_row, w = u - r * per_row;
+                const int b = w / ps.m, j = w - b * ps.m;
+                switch (ps.r) {
+                    case 2: row_butterfly<2, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
+                    case 4: row_butterfly<4, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
+                    case 8: row_butterfly<8, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
+                    default: row_butterfly<16, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // flush: accumulator slot e = q * U + (r * N1/R + b) holds row r, position b*R + q
+    const int RL = p.pass[p.npass - 1].r;
+    const int U = p.RB * (p.N1 / RL);
+    A *part = reinterpret_cast<A *>(p.partial) + (size_t)g * p.N;
+    for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+        const int q = e / U, w = e - q * U;
+        const int r = w / (p.N1 / RL), b = w - r * (p.N1 / RL);
+        const size_t o = (size_t)(blockIdx.x * p.RB + r) * p.N1 + b * RL + q;
+        if constexpr (NPOL == 2) {
+            float4 a = part[o];
+            const float4 d = acc[e];
+            part[o] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+        } else {
+            part[o] += acc[e];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reduce --
+// d_accum[k] += sum over groups of partial[g][posA(k2) * N1 + posB(k1)].
+template <int NPOL>
+__global__ void reduce_kernel(const void *partial, int groups, int N, int N1, int N2,
+                              const int *invA, const int *invB, void *out) {
+    using A = typename Elem<NPOL>::Acc;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int k2 = k & (N2 - 1), k1 = k / N2;
+    const size_t idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
+    const A *pp = reinterpret_cast<const A *>(partial);
+    A *o = reinterpret_cast<A *>(out);
+    if constexpr (NPOL == 2) {
+        float4 s = pp[idx];
+        for (int g = 1; g < groups; g++) {
+            const float4 v = pp[(size_t)g * N + idx];
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        }
+        float4 a = o[k];
+        o[k] = make_float4(a.x + s.x, a.y + s.y, a.z + s.z, a.w + s.w);
+    } else {
+        float s = pp[idx];
+        for (int g = 1; g < groups; g++) s += pp[(size_t)g * N + idx];
+        o[k] += s;
+    }
+}
+
+// ------------------------------------------------------ plan-time tables ---
+// All plan tables are computed in FP64 and rounded once to FP32.
+
+constexpr double kPi = 3.14159265358979323846;
+
+// W_L^m = exp(-2 pi i m / L) for 0 <= m < L.
+__device__ __forceinline__ float2 root_of_unity(long long m, long long L) {
+    const double a = 2.0 * (double)m / (double)L;
+    double s, c;
+    sincospi(a, &s, &c);
+    return make_float2((float)c, (float)-s);
+}
+
+// Pre-filter coefficients, h[i] = w[i] * sinc((i - (L-1)/2) / N) (PFB) or w[i]
+// (direct), with the symmetric window w of length L.
+__global__ void gen_coef_kernel(float *h, int N, int L, int pfb, int window) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    double w = 1.0;
+    if (window != 0 && L > 1) {
+        const double c = cospi(2.0 * (double)i / (double)(L - 1));
+        w = (window == 1) ? 0.5 - 0.5 * c : 0.54 - 0.46 * c;
+    }
+    double v = w;
+    if (pfb) {
+        const double u = ((double)i - 0.5 * (double)(L - 1)) / (double)N;
+        v = (u == 0.0) ? w : w * sinpi(u) / (kPi * u);
+    }
+    h[i] = (float)v;
+}
+
+// Twiddles of one DIF pass: tw[off + j*(r-1) + q-1] = W_lb^(j*q).
+__global__ void gen_pass_tw_kernel(float2 *tw, Pass ps) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = ps.m * (ps.r - 1);
+    if (e >= n) return;
+    const int j = e / (ps.r - 1), q = e - j * (ps.r - 1) + 1;
+    tw[ps.off + e] = root_of_unity((long long)j * q, ps.lb);
+}
+
+// Four-step twiddles in pass-output row order: twZ[pos][n1] = W_N^(n1 * k2(pos)).
+__global__ void gen_twz_kernel(float2 *twZ, int N, int N1, int N2, const int *digrevA) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)N) return;
+    const int pos = (int)(e / N1), n1 = (int)(e - (long long)pos * N1);
+    const long long m = ((long long)n1 * digrevA[pos]) % N;
+    twZ[e] = root_of_unity(m, N);
+}
+
+}  // namespace vspec

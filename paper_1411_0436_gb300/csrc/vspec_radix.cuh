@@ -1,0 +1,124 @@
+// vspec_radix.cuh — complex helpers and small in-register DFTs.
+//
+// An element is either one complex value (float2: re, im) or the two
+// polarisations of the same sample or channel (float4: x.re, x.im, y.re,
+// y.im). Every butterfly applies the same arithmetic to both halves of a
+// float4, so both polarisations share twiddle loads and index arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace vspec {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 csub(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+// (a.re + i a.im) * (w.re + i w.im)
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float4 cmul(float4 a, float2 w) {
+    return make_float4(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x),
+                       fmaf(a.z, w.x, -a.w * w.y), fmaf(a.z, w.y, a.w * w.x));
+}
+
+// multiplication by -i: (re, im) -> (im, -re)
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float4 cmul_mi(float4 a) { return make_float4(a.y, -a.x, a.w, -a.z); }
+
+// multiplication by a twiddle given as compile-time constants (c, s): c + i s
+template <typename T> __device__ __forceinline__ T cmulc(T a, float c, float s) {
+    return cmul(a, make_float2(c, s));
+}
+
+// Constants: cos and sin of multiples of pi/8 (the 16th roots of unity).
+constexpr float kC8 = 0.70710678118654752440f;  // cos(pi/4)
+constexpr float kC16 = 0.92387953251128675613f; // cos(pi/8)
+constexpr float kS16 = 0.38268343236508977173f; // sin(pi/8)
+
+// W_R^q = exp(-2 pi i q / R) applied to a, for R in {8, 16}.
+template <int R, int Q, typename T> __device__ __forceinline__ T twiddle_const(T a) {
+    static_assert(R == 8 || R == 16, "constant twiddles for R = 8, 16");
+    constexpr int q = (R == 8) ? 2 * Q : Q;  // express as a 16th root
+    if constexpr (q == 0) return a;
+    else if constexpr (q == 4) return cmul_mi(a);
+    else if constexpr (q == 2) return cmulc(a, kC8, -kC8);
+    else if constexpr (q == 6) return cmulc(a, -kC8, -kC8);
+    else if constexpr (q == 1) return cmulc(a, kC16, -kS16);
+    else if constexpr (q == 3) return cmulc(a, kS16, -kC16);
+    else if constexpr (q == 5) return cmulc(a, -kS16, -kC16);
+    else return cmulc(a, -kC16, -kS16);  // q == 7
+}
+
+// In-register DFT of R values, natural order in and out:
+//   v[q] <- sum_r v[r] exp(-2 pi i r q / R).
+// R = 8 and 16 split into even- and odd-indexed halves (decimation in time).
+template <int R> struct Dft;
+
+template <> struct Dft<1> {
+    template <typename T> __device__ __forceinline__ static void run(T (&)[1]) {}
+};
+
+template <> struct Dft<2> {
+    template <typename T> __device__ __forceinline__ static void run(T (&v)[2]) {
+        T a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <> struct Dft<4> {
+    template <typename T> __device__ __forceinline__ static void run(T (&v)[4]) {
+        T a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        T c = cadd(v[1], v[3]), d = cmul_mi(csub(v[1], v[3]));
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    }
+};
+
+template <int R> struct DftSplit {
+    template <typename T, int... Q>
+    __device__ __forceinline__ static void combine(T (&v)[R], T (&e)[R / 2], T (&o)[R / 2],
+                                                   std::integer_sequence<int, Q...>) {
+        ((o[Q] = twiddle_const<R, Q>(o[Q])), ...);
+        ((v[Q] = cadd(e[Q], o[Q])), ...);
+        ((v[Q + R / 2] = csub(e[Q], o[Q])), ...);
+    }
+    template <typename T> __device__ __forceinline__ static void run(T (&v)[R]) {
+        T e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; i++) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        Dft<R / 2>::run(e);
+        Dft<R / 2>::run(o);
+        combine(v, e, o, std::make_integer_sequence<int, R / 2>{});
+    }
+};
+
+template <> struct Dft<8> {
+    template <typename T> __device__ __forceinline__ static void run(T (&v)[8]) { DftSplit<8>::run(v); }
+};
+template <> struct Dft<16> {
+    template <typename T> __device__ __forceinline__ static void run(T (&v)[16]) { DftSplit<16>::run(v); }
+};
+
+// Pass descriptor of an in-place decimation-in-frequency pass: blocks of
+// length lb, radix r, m = lb / r butterflies per block, twiddles
+// W_lb^(j*q) stored at tw[off + j*(r-1) + q-1].
+struct Pass {
+    int r;
+    int m;
+    int lb;
+    int off;
+};
+
+}  // namespace vspec

@@ -1,0 +1,234 @@
+"""Python binding of the vspec C ABI (include/vspec.h).
+
+Argument marshalling only: every step of the channelizer runs in the CUDA
+library ``libvspec.so`` built from ``csrc/``. If the library cannot be loaded
+this module raises; there is no CPU fallback. Device buffers are passed as
+torch CUDA tensors (or raw integer device addresses); PyTorch supplies device
+memory and streams and nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+from . import build as _build
+
+PFB, DIRECT = 0, 1
+WIN_RECT, WIN_HANN, WIN_HAMMING = 0, 1, 2
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED = -2
+ERR_ALIGNMENT = -3
+ERR_CUDA = -4
+ERR_OOM = -5
+ERR_DEVICE_TIMEOUT = -6
+
+_lib = None
+
+
+class VspecError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = load()
+        msg = lib.vspec_status_string(status).decode()
+        detail = lib.vspec_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f": {detail}" if detail else ""))
+
+
+def header_path() -> str:
+    return os.path.join(_build.INCLUDE, "vspec.h")
+
+
+def declared_functions() -> list:
+    """Names of the functions include/vspec.h declares."""
+    text = open(header_path()).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vspec_\w+)\s*\(", text)))
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libvspec.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run paper_1411_0436_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        vp, i, cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p
+        lib.vspec_plan_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i]
+        lib.vspec_plan_create.restype = i
+        lib.vspec_plan_destroy.argtypes = [vp]
+        lib.vspec_plan_destroy.restype = i
+        lib.vspec_execute.argtypes = [vp, vp, i, vp, vp]
+        lib.vspec_execute.restype = i
+        lib.vspec_dump.argtypes = [vp, vp, vp, vp]
+        lib.vspec_dump.restype = i
+        lib.vspec_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i)]
+        lib.vspec_plan_info.restype = i
+        lib.vspec_plan_set_profiling.argtypes = [vp, i]
+        lib.vspec_plan_set_profiling.restype = i
+        lib.vspec_plan_kernel_stats.argtypes = [vp, i, i, ctypes.POINTER(cp), ctypes.POINTER(ctypes.c_longlong),
+                                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+        lib.vspec_plan_kernel_stats.restype = i
+        lib.vspec_status_string.argtypes = [i]
+        lib.vspec_status_string.restype = cp
+        lib.vspec_last_error.argtypes = []
+        lib.vspec_last_error.restype = cp
+        _lib = lib
+    return _lib
+
+
+def _addr(x) -> Optional[int]:
+    """Device or host address of a tensor / array / int (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- the C functions, same names -------------------------------------------
+
+def vspec_plan_create(nchan: int, ntaps: int, npol: int, mode: int, window: int) -> int:
+    h = ctypes.c_void_p()
+    st = load().vspec_plan_create(ctypes.byref(h), nchan, ntaps, npol, mode, window)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_create")
+    return h.value
+
+
+def vspec_plan_destroy(plan: int) -> None:
+    st = load().vspec_plan_destroy(plan)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_destroy")
+
+
+def vspec_execute(plan: int, d_in, nspectra: int, d_accum, stream=None) -> None:
+    st = load().vspec_execute(plan, _addr(d_in), nspectra, _addr(d_accum), _stream(stream))
+    if st != OK:
+        raise VspecError(st, "vspec_execute")
+
+
+def vspec_dump(plan: int, d_accum, h_out=None, stream=None) -> None:
+    st = load().vspec_dump(plan, _addr(d_accum), _addr(h_out), _stream(stream))
+    if st != OK:
+        raise VspecError(st, "vspec_dump")
+
+
+def vspec_plan_info(plan: int):
+    sb = ctypes.c_size_t()
+    hp = ctypes.c_int()
+    st = load().vspec_plan_info(plan, ctypes.byref(sb), ctypes.byref(hp))
+    if st != OK:
+        raise VspecError(st, "vspec_plan_info")
+    return int(sb.value), int(hp.value)
+
+
+def vspec_plan_set_profiling(plan: int, enable: bool) -> None:
+    st = load().vspec_plan_set_profiling(plan, 1 if enable else 0)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_set_profiling")
+
+
+def vspec_plan_kernel_stats(plan: int, reset: bool = False) -> list:
+    """[(name, launches, spectra, total_ms)] for every kernel kind."""
+    lib = load()
+    out = []
+    kind = 0
+    while True:
+        name = ctypes.c_char_p()
+        n = ctypes.c_longlong()
+        sp = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        st = lib.vspec_plan_kernel_stats(plan, kind, 0, ctypes.byref(name), ctypes.byref(n),
+                                         ctypes.byref(sp), ctypes.byref(ms))
+        if st == ERR_INVALID_ARG:
+            break
+        if st != OK:
+            raise VspecError(st, "vspec_plan_kernel_stats")
+        out.append((name.value.decode(), int(n.value), int(sp.value), float(ms.value)))
+        kind += 1
+    if reset:
+        vspec_plan_set_profiling(plan, True)
+    return out
+
+
+def vspec_status_string(status: int) -> str:
+    return load().vspec_status_string(status).decode()
+
+
+# ---- convenience wrapper ------------------------------------------------------
+
+class Plan:
+    """Owns one vspec plan; checks tensor shapes before calling the library."""
+
+    def __init__(self, nchan: int, ntaps: int = 8, npol: int = 2, mode: int = PFB,
+                 window: int = WIN_HANN):
+        self.nchan, self.ntaps, self.npol, self.mode, self.window = nchan, ntaps, npol, mode, window
+        self.taps_used = 1 if mode == DIRECT else ntaps
+        self.handle = vspec_plan_create(nchan, ntaps, npol, mode, window)
+
+    @property
+    def out_floats(self) -> int:
+        return self.nchan * (4 if self.npol == 2 else 1)
+
+    def input_bytes(self, nspectra: int) -> int:
+        return (nspectra + self.taps_used - 1) * self.nchan * self.npol * 2
+
+    def execute(self, d_in, nspectra: int, d_accum, stream=None) -> None:
+        if hasattr(d_in, "is_cuda"):
+            if not d_in.is_cuda or not d_in.is_contiguous():
+                raise ValueError("d_in must be a contiguous CUDA tensor")
+            if d_in.numel() * d_in.element_size() < self.input_bytes(nspectra):
+                raise ValueError("d_in is smaller than (nspectra + P - 1) * nchan samples")
+        if hasattr(d_accum, "is_cuda"):
+            if not d_accum.is_cuda or not d_accum.is_contiguous() or d_accum.numel() < self.out_floats:
+                raise ValueError("d_accum must be a contiguous CUDA float tensor of nchan*(4|1) floats")
+        vspec_execute(self.handle, d_in, nspectra, d_accum, stream)
+
+    def dump(self, d_accum, h_out=None, stream=None) -> None:
+        vspec_dump(self.handle, d_accum, h_out, stream)
+
+    def info(self):
+        return vspec_plan_info(self.handle)
+
+    def set_profiling(self, enable: bool = True) -> None:
+        vspec_plan_set_profiling(self.handle, enable)
+
+    def kernel_stats(self, reset: bool = False) -> list:
+        return vspec_plan_kernel_stats(self.handle, reset)
+
+    def close(self) -> None:
+        if self.handle:
+            vspec_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,170 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Inputs come from the shared seeded generators; the oracle never sees anything
+the CUDA path produced. Sizes are chosen so the oracle finishes in seconds
+while the GPU runs span several tiles, several scratch chunks and ragged
+tails; the full workload sizes are in test_gpu_workloads.py.
+"""
+import numpy as np
+import pytest
+
+from parity_util import RTOL_FP32, assert_close
+from paper_1411_0436_gb300 import workloads
+from paper_1411_0436_gb300.workloads import DIRECT, PFB, WIN_HAMMING, WIN_HANN, WIN_RECT, Bank, Tone
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run_gpu(bank: Bank, x: np.ndarray, repeat: int = 1) -> np.ndarray:
+    from paper_1411_0436_gb300.vspec import Plan
+    with Plan(bank.nchan, bank.ntaps, bank.npol, bank.mode, bank.window) as plan:
+        d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        for _ in range(repeat):
+            plan.execute(d_in, bank.nspectra, acc)
+        torch.cuda.synchronize()
+        out = acc.cpu().numpy().astype(np.float64)
+    return out.reshape(bank.nchan, 4) if bank.npol == 2 else out
+
+
+def run_oracle(oracle_mod, bank: Bank, x: np.ndarray) -> np.ndarray:
+    return oracle_mod.channelize(x, bank.nchan, bank.ntaps, bank.npol, bank.nspectra,
+                                 bank.mode, bank.window)
+
+
+SMALL = [
+    # nchan, ntaps, npol, mode, window, nspectra
+    (16, 8, 2, PFB, WIN_HANN, 5),
+    (16, 1, 1, DIRECT, WIN_RECT, 3),
+    (64, 8, 1, PFB, WIN_HANN, 9),
+    (256, 8, 2, PFB, WIN_HANN, 17),
+    (256, 3, 2, PFB, WIN_HAMMING, 11),
+    (512, 16, 2, PFB, WIN_HANN, 20),
+    (1024, 8, 1, PFB, WIN_HANN, 64),
+    (1024, 5, 2, PFB, WIN_RECT, 13),
+    (2048, 8, 2, PFB, WIN_HANN, 33),
+    (4096, 1, 2, DIRECT, WIN_RECT, 9),
+    (4096, 8, 2, PFB, WIN_HANN, 19),
+    (8192, 2, 1, PFB, WIN_HANN, 7),
+    (8192, 1, 2, DIRECT, WIN_HANN, 6),
+    (16384, 8, 2, PFB, WIN_HANN, 10),
+    (32768, 8, 2, PFB, WIN_HANN, 67),   # two scratch chunks, ragged second chunk
+    (32768, 12, 2, PFB, WIN_HAMMING, 5),
+    (65536, 8, 2, PFB, WIN_HANN, 4),
+    (65536, 4, 1, PFB, WIN_HANN, 6),
+    (131072, 1, 2, DIRECT, WIN_RECT, 3),
+    (262144, 8, 2, PFB, WIN_HANN, 2),
+    (524288, 1, 2, DIRECT, WIN_RECT, 2),
+    (1 << 20, 1, 2, DIRECT, WIN_RECT, 1),
+]
+
+
+@pytest.mark.parametrize("cfg", SMALL, ids=lambda c: f"N{c[0]}_P{c[1]}_pol{c[2]}_m{c[3]}_w{c[4]}_S{c[5]}")
+def test_matches_oracle(oracle_mod, cfg):
+    n, p, npol, mode, win, s = cfg
+    tones = (Tone(25.0, n * 0.3 + 0.4, (0, 1)),) if n >= 64 else ()
+    bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3 if npol == 2 else 0.0, tones=tones)
+    x = workloads.generate(bank, 1000 + n + p)
+    g = run_gpu(bank, x)
+    o = run_oracle(oracle_mod, bank, x)
+    assert_close(g, o, what=str(cfg))
+
+
+def test_impulse_is_bit_exact_for_every_int8_value():
+    """Direct mode, impulse at the first sample: every channel is exactly
+    |v|^2 (and the cross terms are exact integers), which pins the int8 unpack."""
+    n = 64
+    bank = Bank(n, 1, 2, DIRECT, WIN_RECT, 1)
+    for v in range(-128, 128):
+        x = np.zeros((n, 2, 2), np.int8)
+        x[0, 0] = (v, 127)    # X[k] = v + 127 i
+        x[0, 1] = (-128, v)   # Y[k] = -128 + v i
+        g = run_gpu(bank, x)
+        expect = np.array([v * v + 127 * 127, 128 * 128 + v * v,
+                           -128 * v + 127 * v, 127 * -128 - v * v], np.float64)
+        assert np.array_equal(g, np.broadcast_to(expect, g.shape)), v
+
+
+@pytest.mark.parametrize("n,k0", [(1024, 123), (32768, 3277), (32768, 0), (131072, 26214)])
+def test_tone_lands_in_its_channel(oracle_mod, n, k0):
+    """Channel indexing: a strong tone at an integer bin is the argmax (same bin
+    as the oracle), bit-exact as an index."""
+    bank = Bank(n, 8, 2, PFB, WIN_HANN, 3, sigma=5.0, tones=(Tone(60.0, float(k0), (0, 1)),))
+    x = workloads.generate(bank, 7 + k0)
+    g = run_gpu(bank, x)
+    o = run_oracle(oracle_mod, bank, x)
+    assert int(np.argmax(g[:, 0])) == k0 == int(np.argmax(o[:, 0]))
+    assert int(np.argmax(g[:, 1])) == k0
+
+
+def test_accumulates_and_dump_clears():
+    from paper_1411_0436_gb300.vspec import Plan
+    bank = Bank(4096, 8, 2, PFB, WIN_HANN, 5)
+    x = workloads.generate(bank, 3)
+    once = run_gpu(bank, x)
+    with Plan(bank.nchan, bank.ntaps, bank.npol, bank.mode, bank.window) as plan:
+        d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        plan.execute(d_in, bank.nspectra, acc)
+        plan.execute(d_in, bank.nspectra, acc)
+        h = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
+        plan.dump(acc, h)
+        torch.cuda.synchronize()
+        twice = h.numpy().astype(np.float64).reshape(-1, 4)
+        assert torch.count_nonzero(acc).item() == 0
+        plan.execute(d_in, 0, acc)  # no-op
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(acc).item() == 0
+    assert np.max(np.abs(twice - 2 * once)) <= RTOL_FP32 * np.max(np.abs(twice))
+
+
+def test_repeat_runs_are_bitwise_identical():
+    bank = Bank(32768, 8, 2, PFB, WIN_HANN, 70, rho=0.3)
+    x = workloads.generate(bank, 11)
+    a = run_gpu(bank, x)
+    b = run_gpu(bank, x)
+    assert np.array_equal(a, b)
+
+
+def test_streaming_calls_equal_one_call(oracle_mod):
+    """Consecutive calls over inputs overlapped by (P-1)*N samples add up to
+    one call over the whole run (the paper's per-iteration loop)."""
+    from paper_1411_0436_gb300.vspec import Plan
+    bank = Bank(8192, 8, 2, PFB, WIN_HANN, 24, rho=0.3)
+    x = workloads.generate(bank, 21)
+    whole = run_gpu(bank, x)
+    n, P = bank.nchan, bank.ntaps
+    with Plan(n, P, 2, PFB, WIN_HANN) as plan:
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        for s0, cnt in [(0, 10), (10, 9), (19, 5)]:
+            part = np.ascontiguousarray(x[s0 * n:(s0 + cnt + P - 1) * n])
+            plan.execute(torch.from_numpy(part.view(np.uint8).reshape(-1)).cuda(), cnt, acc)
+        torch.cuda.synchronize()
+        got = acc.cpu().numpy().astype(np.float64).reshape(-1, 4)
+    assert_close(got, run_oracle(oracle_mod, bank, x))
+    assert_close(got, whole)
+
+
+def test_error_paths_on_device():
+    from paper_1411_0436_gb300 import vspec
+    with vspec.Plan(1024, 8, 2, PFB, WIN_HANN) as plan:
+        buf = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+        acc = torch.zeros(4096, dtype=torch.float32, device="cuda")
+        lib = vspec.load()
+        s = torch.cuda.current_stream().cuda_stream
+        assert lib.vspec_execute(plan.handle, buf.data_ptr() + 4, 1, acc.data_ptr(), s) == vspec.ERR_ALIGNMENT
+        assert lib.vspec_execute(plan.handle, buf.data_ptr(), 1, acc.data_ptr() + 4, s) == vspec.ERR_ALIGNMENT
+        assert lib.vspec_execute(plan.handle, buf.data_ptr(), -1, acc.data_ptr(), s) == vspec.ERR_INVALID_ARG
+        assert lib.vspec_dump(plan.handle, acc.data_ptr() + 8, None, s) == vspec.ERR_ALIGNMENT
+        sb, hp = plan.info()
+        assert sb > 0 and hp == 1
+    with pytest.raises(vspec.VspecError) as e:
+        vspec.Plan(1 << 20, 8, 2, PFB, WIN_HANN)
+    assert e.value.status == vspec.ERR_UNSUPPORTED

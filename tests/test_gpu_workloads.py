@@ -1,0 +1,37 @@
+"""Full-size workloads: every bank of the five workload configurations, GPU vs
+the FP64 oracle over all channels, in the launch configuration the benchmark
+uses (one plan, one vspec_execute over all spectra of the dump)."""
+import time
+
+import numpy as np
+import pytest
+
+from parity_util import assert_close
+from paper_1411_0436_gb300 import workloads
+from test_gpu_parity import run_gpu, run_oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CASES = [(name, i) for name in ("c1", "c2", "c3", "c4", "c5")
+         for i in range(len(workloads.CONFIGS[name]))]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("name,idx", CASES, ids=[f"{n}_bank{i}" for n, i in CASES])
+def test_workload_matches_oracle(oracle_mod, name, idx):
+    bank = workloads.CONFIGS[name][idx]
+    x = workloads.generate(bank, workloads.config_seed(name, idx))
+    t0 = time.time()
+    g = run_gpu(bank, x)
+    t1 = time.time()
+    o = run_oracle(oracle_mod, bank, x)
+    t2 = time.time()
+    m = assert_close(g, o, what=f"{name}[{idx}]")
+    print(f"\n{name}[{idx}] N={bank.nchan} S={bank.nspectra}: normalised max err {m['pure']:.3e}, "
+          f"tolerance use {m['ratio']:.3f}, gpu {t1 - t0:.2f}s oracle {t2 - t1:.1f}s")
