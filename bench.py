@@ -49,9 +49,9 @@ def _peaks():
 
 
 def source_hash() -> str:
+    """Hash of the device-code sources (the kernels an ncu capture measured)."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1411_0436_gb300", "csrc", "*")))
-    files.append(os.path.join(ROOT, "include", "vspec.h"))
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1411_0436_gb300", "csrc", "*.cuh")))
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
