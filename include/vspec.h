@@ -146,6 +146,35 @@ VSPEC_API vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int r
                                                const char **name, long long *launches,
                                                long long *spectra, double *total_ms);
 
+/*
+ * Allocation-free variant of vspec_execute. The paper has no counterpart: it
+ * is for callers that cannot call cudaMalloc, such as a host application that
+ * owns every byte of device memory through its own pool, or a real-time
+ * capture loop in which an allocation (which can synchronise the whole
+ * device) would stall the data path and drop samples.
+ *
+ * It computes exactly what a plan created with the same (nchan, ntaps, npol,
+ * mode, window) computes in vspec_execute, accumulating into d_accum with the
+ * same input and output layouts, but allocates nothing: coefficients,
+ * twiddles, chunk scratch and partial sums live in one fixed 20 MiB device
+ * array inside this library, which every GPU that loads the library holds
+ * until the process exits. Limits: nchan <= 32768 (larger sizes return
+ * VSPEC_ERR_UNSUPPORTED with the reason in vspec_last_error); all other
+ * arguments and errors are as for vspec_plan_create and vspec_execute.
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address and sets kernel attributes; make that first call
+ * before any stream capture. A call whose (nchan, ntaps, npol, mode, window)
+ * differs from the previous call on that device rebuilds the tables in the
+ * array on `stream`. Every call shares the array, which keeps the last
+ * call's contents, so calls that overlap on the GPU race: serialise them
+ * (one stream, or synchronise between calls). Host threads are serialised by
+ * an internal lock.
+ */
+VSPEC_API vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int ntaps, int npol,
+                                             vspec_mode mode, vspec_window window, int nspectra,
+                                             float *d_accum, void *stream);
+
 /* Static, human-readable text for a status code. */
 VSPEC_API const char *vspec_status_string(vspec_status status);
 

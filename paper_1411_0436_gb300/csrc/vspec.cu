@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -506,3 +507,279 @@ vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *st
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free path ===
+//
+// vspec_execute_noalloc runs the same kernels as vspec_execute, but keeps its
+// coefficients, twiddle tables, digit-reversal maps, chunk scratch and
+// partial sums in one fixed device array declared below instead of memory
+// from cudaMalloc. It exists for callers that cannot allocate device memory:
+// a host application that owns every byte of device memory through its own
+// pool, or a real-time capture loop where a cudaMalloc (which can synchronise
+// the whole device) would stall the data path and drop samples. The paper
+// has no counterpart.
+
+namespace {
+
+constexpr int kNoAllocMaxChan = 32768;  // largest nchan the fixed array holds
+constexpr int kNoAllocChunk = 16;       // spectra per scratch chunk
+constexpr int kNoAllocGroups = 16;      // kernel-B spectrum groups
+constexpr int kMaxDevices = 64;
+
+// byte offsets inside the array (every region 256-byte aligned)
+constexpr size_t kNaCoef = 0;                                            // 16 * N floats
+constexpr size_t kNaTwA = kNaCoef + 16ull * kNoAllocMaxChan * 4;         // < N float2
+constexpr size_t kNaTwB = kNaTwA + (size_t)kNoAllocMaxChan * 8;          // < N float2
+constexpr size_t kNaTwZ = kNaTwB + (size_t)kNoAllocMaxChan * 8;          // N float2
+constexpr size_t kNaInts = kNaTwZ + (size_t)kNoAllocMaxChan * 8;         // kA, invA, invB
+constexpr size_t kNaZ = kNaInts + 3ull * kNoAllocMaxChan * 4;            // chunk scratch
+constexpr size_t kNaPartial = kNaZ + (size_t)kNoAllocChunk * kNoAllocMaxChan * 16;
+constexpr size_t kNoAllocBytes = kNaPartial + (size_t)kNoAllocGroups * kNoAllocMaxChan * 16;
+
+// The fixed scratch: 20 MiB, held by every GPU that loads this library until
+// the process exits. Host code must not pass this name to a kernel: on the
+// host it is only a stand-in; its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocCfg {
+    int N, P, npol, mode, window;
+    int N1, N2, C, PT, PPT, TA, RB, TB, groups_b, sc_max, occA;
+    int nA, nB;
+    Pass passA[vspec::kMaxPasses], passB[vspec::kMaxPasses];
+    const void *kA, *kB, *kR;
+    size_t smemA, smemB;
+};
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_noalloc_scratch
+    int num_sms = 0;
+    bool tables_valid = false;
+    int key[5] = {0, 0, 0, 0, 0};   // (N, P, npol, mode, window) of the tables
+};
+
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kMaxDevices];
+
+// Digit-reversal maps of both DFT factors, computed on the device:
+// kA[pos] = k2 held at row position pos, invA[k2] = pos, invB[k1] = posB.
+__global__ void noalloc_digrev_kernel(int *kA, int *invA, int *invB, int N2, int N1,
+                                      NoAllocCfg cfg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N2) {
+        int rem = e, lb = N2, k = 0, scale = 1;
+        for (int i = 0; i < cfg.nA; i++) {
+            const int m = lb / cfg.passA[i].r, q = rem / m;
+            rem -= q * m;
+            k += q * scale;
+            scale *= cfg.passA[i].r;
+            lb = m;
+        }
+        kA[e] = k;
+        invA[k] = e;
+    }
+    if (e < N1) {
+        int rem = e, lb = N1, k = 0, scale = 1;
+        for (int i = 0; i < cfg.nB; i++) {
+            const int m = lb / cfg.passB[i].r, q = rem / m;
+            rem -= q * m;
+            k += q * scale;
+            scale *= cfg.passB[i].r;
+            lb = m;
+        }
+        invB[k] = e;
+    }
+}
+
+// The same size choices as build_plan, restricted to nchan <= 32768.
+vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
+    const int N = c->N;
+    const bool pfb = c->mode == VSPEC_PFB;
+    const int PT = c->P <= 1 ? 1 : c->P <= 2 ? 2 : c->P <= 4 ? 4 : c->P <= 8 ? 8 : 16;
+    const int cmin = c->npol == 2 ? 16 : 32;
+    int n2max = !pfb ? 4096 / cmin : PT <= 8 ? 1024 / cmin : 512 / cmin;
+    int N2 = 1;
+    while (N / N2 > kRowElems && N2 < n2max) N2 *= 2;
+    const int N1 = N / N2;
+    int C = std::min(std::max(cmin, 256 / N2), N1);
+    const int pts = N2 * C;
+    c->TA = std::min(512, pts);
+    c->PPT = pts / c->TA;
+    c->N1 = N1;
+    c->N2 = N2;
+    c->C = C;
+    c->PT = PT;
+    c->kA = c->npol == 2 ? pick_kernel_a<2>(PT, c->PPT) : pick_kernel_a<1>(PT, c->PPT);
+    if (!c->kA) {
+        g_last_error = "no kernel instance for this tap count and size";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    c->kB = c->npol == 2 ? (const void *)vspec::rowfft_detect_kernel<2> : (const void *)vspec::rowfft_detect_kernel<1>;
+    c->kR = c->npol == 2 ? (const void *)vspec::reduce_kernel<2> : (const void *)vspec::reduce_kernel<1>;
+    const int capA = vspec::col_radix_cap(c->npol, PT, c->PPT);
+    const int e = ilog2(N), e2 = ilog2(N2);
+    // pass lists as in radix_list / make_passes, in fixed arrays (no heap)
+    auto fill = [](Pass *ps, int L, int ebits, int maxbits) {
+        int np = ebits == 0 ? 0 : (ebits + maxbits - 1) / maxbits;
+        int lb = L, off = 0;
+        for (int i = 0; i < np; i++) {
+            const int r = 1 << (ebits / np + (i < ebits % np ? 1 : 0));
+            ps[i].r = r;
+            ps[i].lb = lb;
+            ps[i].m = lb / r;
+            ps[i].off = off;
+            off += ps[i].m * (r - 1);
+            lb /= r;
+        }
+        return np;
+    };
+    c->nA = fill(c->passA, N2, e2, capA == 16 ? 4 : capA == 8 ? 3 : 2);
+    c->nB = fill(c->passB, N1, e - e2, 4);
+    c->RB = std::max(1, std::min(N2, kRowElems / N1));
+    int maxb = 1;
+    for (int i = 0; i < c->nB; i++) maxb = std::max(maxb, c->RB * (N1 / c->passB[i].r));
+    c->TB = std::min(256, std::max(32, maxb));
+    const size_t elem = c->npol == 2 ? sizeof(float4) : sizeof(float2);
+    const size_t accel = c->npol == 2 ? sizeof(float4) : sizeof(float);
+    c->smemA = (size_t)PT * N2 * C * elem;
+    c->smemB = (size_t)c->RB * (N1 + (N1 >> 4)) * elem + (size_t)c->RB * N1 * accel;
+    VSPEC_CUDA(cudaFuncSetAttribute(c->kA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smemA));
+    VSPEC_CUDA(cudaFuncSetAttribute(c->kB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smemB));
+    int occB = 1;
+    VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occA, c->kA, c->TA, c->smemA));
+    VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, c->kB, c->TB, c->smemB));
+    c->sc_max = (int)std::min<size_t>(kNoAllocChunk, (size_t)kNoAllocChunk * kNoAllocMaxChan / N);
+    const int blocksB = N2 / c->RB;
+    c->groups_b = std::max(1, std::min(std::min(kNoAllocGroups, c->sc_max),
+                                       (num_sms * std::max(1, occB) + blocksB - 1) / blocksB));
+    return VSPEC_OK;
+}
+
+}  // namespace
+
+extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int ntaps, int npol,
+                                              vspec_mode mode, vspec_window window, int nspectra,
+                                              float *d_accum, void *stream) {
+    if (!d_in || !d_accum || nspectra < 0) return VSPEC_ERR_INVALID_ARG;
+    if (!is_pow2(nchan) || nchan < 16 || nchan > (1 << 20)) return VSPEC_ERR_INVALID_ARG;
+    if (npol != 1 && npol != 2) return VSPEC_ERR_INVALID_ARG;
+    if (mode != VSPEC_PFB && mode != VSPEC_DIRECT) return VSPEC_ERR_INVALID_ARG;
+    if (window != VSPEC_WIN_RECT && window != VSPEC_WIN_HANN && window != VSPEC_WIN_HAMMING)
+        return VSPEC_ERR_INVALID_ARG;
+    if (mode == VSPEC_PFB && (ntaps < 1 || ntaps > 16)) return VSPEC_ERR_INVALID_ARG;
+    if (mode == VSPEC_DIRECT && (ntaps < 0 || ntaps > 1)) return VSPEC_ERR_INVALID_ARG;
+    if (nchan > kNoAllocMaxChan) {
+        g_last_error = "vspec_execute_noalloc: nchan " + std::to_string(nchan) +
+                       " exceeds the 32768-channel limit of its fixed scratch";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    if (!aligned16(d_in) || !aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
+    if (nspectra == 0) return VSPEC_OK;
+
+    int dev = 0;
+    VSPEC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return VSPEC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        // once per device, with that device current: the array's device address
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        VSPEC_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        d.base = static_cast<unsigned char *>(ptr);
+        d.ready = true;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+
+    NoAllocCfg c{};
+    c.N = nchan;
+    c.P = mode == VSPEC_PFB ? ntaps : 1;
+    c.npol = npol;
+    c.mode = mode;
+    c.window = window;
+    vspec_status r = noalloc_configure(&c, d.num_sms);
+    if (r != VSPEC_OK) return r;
+
+    float *coef = reinterpret_cast<float *>(d.base + kNaCoef);
+    float2 *twA = reinterpret_cast<float2 *>(d.base + kNaTwA);
+    float2 *twB = reinterpret_cast<float2 *>(d.base + kNaTwB);
+    float2 *twZ = reinterpret_cast<float2 *>(d.base + kNaTwZ);
+    int *kA = reinterpret_cast<int *>(d.base + kNaInts);
+    int *invA = kA + kNoAllocMaxChan;
+    int *invB = invA + kNoAllocMaxChan;
+    void *Z = d.base + kNaZ;
+    void *partial = d.base + kNaPartial;
+
+    // The array keeps the last call's tables; rebuild them when the problem changes.
+    const int key[5] = {c.N, c.P, c.npol, c.mode, c.window};
+    if (!d.tables_valid || std::memcmp(key, d.key, sizeof(key)) != 0) {
+        d.tables_valid = false;
+        const int N = c.N, Lc = c.P * N;
+        vspec::gen_coef_kernel<<<(Lc + 255) / 256, 256, 0, st>>>(coef, N, Lc, mode == VSPEC_PFB ? 1 : 0, window);
+        for (int i = 0; i < c.nA; i++)
+            if (c.passA[i].m * (c.passA[i].r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(c.passA[i].m * (c.passA[i].r - 1) + 255) / 256, 256, 0, st>>>(twA, c.passA[i]);
+        for (int i = 0; i < c.nB; i++)
+            if (c.passB[i].m * (c.passB[i].r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(c.passB[i].m * (c.passB[i].r - 1) + 255) / 256, 256, 0, st>>>(twB, c.passB[i]);
+        noalloc_digrev_kernel<<<(std::max(c.N1, c.N2) + 255) / 256, 256, 0, st>>>(kA, invA, invB, c.N2, c.N1, c);
+        vspec::gen_twz_kernel<<<(N + 255) / 256, 256, 0, st>>>(twZ, N, c.N1, c.N2, kA);
+        VSPEC_CUDA(cudaGetLastError());
+        std::memcpy(d.key, key, sizeof(key));
+        d.tables_valid = true;
+    }
+
+    // partial sums must start at zero on every call
+    const size_t accel = npol == 2 ? sizeof(float4) : sizeof(float);
+    VSPEC_CUDA(cudaMemsetAsync(partial, 0, (size_t)c.groups_b * c.N * accel, st));
+
+    vspec::ColParams ca;
+    ca.in = d_in;
+    ca.coef = coef;
+    ca.twA = twA;
+    ca.twZ = twZ;
+    ca.Z = Z;
+    ca.N = c.N;
+    ca.N1 = c.N1;
+    ca.N2 = c.N2;
+    ca.C = c.C;
+    ca.P = c.P;
+    ca.npass = c.nA;
+    for (int i = 0; i < c.nA; i++) ca.pass[i] = c.passA[i];
+    vspec::RowParams cb;
+    cb.Z = Z;
+    cb.partial = partial;
+    cb.twB = twB;
+    cb.N = c.N;
+    cb.N1 = c.N1;
+    cb.N2 = c.N2;
+    cb.RB = c.RB;
+    cb.npass = c.nB;
+    for (int i = 0; i < c.nB; i++) cb.pass[i] = c.passB[i];
+    cb.groups = c.groups_b;
+
+    const int blocksA = c.N1 / c.C;
+    const int targetA = d.num_sms * std::max(1, c.occA);
+    const int sc_full = std::min(nspectra, c.sc_max);
+    for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
+        const int sc = std::min(sc_full, nspectra - s0);
+        const int ga = std::max(1, std::min((targetA + blocksA - 1) / blocksA, sc));
+        ca.s0 = s0;
+        ca.sc = sc;
+        ca.groups = ga;
+        void *argsA[] = {&ca};
+        VSPEC_CUDA(cudaLaunchKernel(c.kA, dim3(blocksA, ga), dim3(c.TA), argsA, c.smemA, st));
+        cb.sc = sc;
+        void *argsB[] = {&cb};
+        VSPEC_CUDA(cudaLaunchKernel(c.kB, dim3(c.N2 / c.RB, c.groups_b), dim3(c.TB), argsB, c.smemB, st));
+    }
+    const void *part = partial;
+    int groups = c.groups_b, N = c.N, N1 = c.N1, N2 = c.N2;
+    const int *ia = invA, *ib = invB;
+    void *outp = d_accum;
+    void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
+    VSPEC_CUDA(cudaLaunchKernel(c.kR, dim3((c.N + 255) / 256), dim3(256), argsR, 0, st));
+    return VSPEC_OK;
+}

@@ -75,6 +75,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_kernel_stats.argtypes = [vp, i, i, ctypes.POINTER(cp), ctypes.POINTER(ctypes.c_longlong),
                                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
         lib.vspec_plan_kernel_stats.restype = i
+        lib.vspec_execute_noalloc.argtypes = [vp, i, i, i, i, i, i, vp, vp]
+        lib.vspec_execute_noalloc.restype = i
         lib.vspec_status_string.argtypes = [i]
         lib.vspec_status_string.restype = cp
         lib.vspec_last_error.argtypes = []
@@ -169,6 +171,15 @@ def vspec_plan_kernel_stats(plan: int, reset: bool = False) -> list:
     if reset:
         vspec_plan_set_profiling(plan, True)
     return out
+
+
+def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, window: int,
+                          nspectra: int, d_accum, stream=None) -> None:
+    """Allocation-free channelization (no plan, no cudaMalloc); see include/vspec.h."""
+    st = load().vspec_execute_noalloc(_addr(d_in), nchan, ntaps, npol, mode, window, nspectra,
+                                      _addr(d_accum), _stream(stream))
+    if st != OK:
+        raise VspecError(st, "vspec_execute_noalloc")
 
 
 def vspec_status_string(status: int) -> str:
