@@ -81,6 +81,17 @@ typedef struct vspec_plan vspec_plan;
 VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
                                vspec_mode mode, vspec_window window);
 
+/* Plan flags for vspec_plan_create_ex. */
+#define VSPEC_PLAN_TWO_KERNEL 1u /* use the general two-kernel path even where the one-pass
+                                    fused path applies (for comparison and testing) */
+
+/*
+ * vspec_plan_create with flags (a bitwise OR of VSPEC_PLAN_* values; 0 gives
+ * vspec_plan_create). Unknown flag bits return VSPEC_ERR_INVALID_ARG.
+ */
+VSPEC_API vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int npol,
+                                            vspec_mode mode, vspec_window window, unsigned flags);
+
 /* Release a plan and all device memory it owns. NULL is accepted. The caller
  * must make sure no work using the plan is still running on any stream. */
 VSPEC_API vspec_status vspec_plan_destroy(vspec_plan *plan);

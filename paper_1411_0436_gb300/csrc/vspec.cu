@@ -16,6 +16,8 @@
 #include <vector>
 
 #include "vspec.h"
+#include "vspec_fused.cuh"
+#include "vspec_fused_w.cuh"
 #include "vspec_kernels.cuh"
 
 using vspec::Pass;
@@ -107,6 +109,12 @@ struct vspec_plan {
     void *Z = nullptr, *partial = nullptr;
     size_t scratch_bytes = 0;
     const void *kernelA = nullptr, *kernelB = nullptr, *kernelR = nullptr;
+    // fused one-pass path (dual-pol, 2048..32768 channels)
+    bool fused = false, fused_w = false;
+    int logn1 = 0, cluster = 1, nclusters = 1;
+    size_t smemF = 0;
+    const void *kernelF = nullptr;
+    unsigned flags = 0;
     // instrumentation (vspec_plan_set_profiling)
     struct Rec {
         int kind;
@@ -136,8 +144,8 @@ template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
     return nullptr;
 }
 
-constexpr int kNumKinds = 3;
-const char *const kKindNames[kNumKinds] = {"fir_colfft", "rowfft_detect", "reduce"};
+constexpr int kNumKinds = 4;
+const char *const kKindNames[kNumKinds] = {"fir_colfft", "rowfft_detect", "reduce", "fused_channelize"};
 
 void release_records(vspec_plan *p) {
     for (auto &r : p->recs) {
@@ -156,16 +164,34 @@ cudaError_t take_event(vspec_plan *p, cudaEvent_t *ev) {
     return cudaEventCreate(ev);
 }
 
-// Launch one kernel on st; in profiling mode bracket it with events.
+// Launch one kernel on st (as clusters of `cluster` CTAs if cluster > 1); in
+// profiling mode bracket it with events.
 vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 grid, dim3 block,
-                    void **args, size_t smem, cudaStream_t st) {
+                    void **args, size_t smem, cudaStream_t st, int cluster = 0) {
     vspec_plan::Rec r{kind, spectra, nullptr, nullptr};
     if (p->profiling) {
         VSPEC_CUDA(take_event(p, &r.start));
         VSPEC_CUDA(take_event(p, &r.stop));
         VSPEC_CUDA(cudaEventRecord(r.start, st));
     }
-    cudaError_t e = cudaLaunchKernel(fn, grid, block, args, smem, st);
+    cudaError_t e;
+    if (cluster > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+    } else {
+        e = cudaLaunchKernel(fn, grid, block, args, smem, st);
+    }
     if (e != cudaSuccess) {
         if (p->profiling) {
             p->event_pool.push_back(r.start);
@@ -178,6 +204,23 @@ vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 g
         p->recs.push_back(r);
     }
     return VSPEC_OK;
+}
+
+const void *pick_kernel_fused(int logn1, int pt) {
+    using namespace vspec::fused;
+    switch (logn1 * 100 + pt) {
+        case 401: return (const void *)fused_kernel<4, 1>;
+        case 408: return (const void *)fused_kernel<4, 8>;
+        case 501: return (const void *)fused_kernel<5, 1>;
+        case 508: return (const void *)fused_kernel<5, 8>;
+        case 601: return (const void *)fused_kernel<6, 1>;
+        case 608: return (const void *)fused_kernel<6, 8>;
+        case 701: return (const void *)fused_kernel<7, 1>;
+        case 708: return (const void *)fused_kernel<7, 8>;
+        case 801: return (const void *)fused_kernel<8, 1>;
+        case 808: return (const void *)fused_kernel<8, 8>;
+    }
+    return nullptr;
 }
 
 void free_plan(vspec_plan *p) {
@@ -212,10 +255,109 @@ vspec_status dev_alloc(void **ptr, size_t bytes, size_t *total) {
 constexpr size_t kScratchBudget = 32u << 20;
 constexpr int kRowElems = 2048;  // target row-DFT elements per kernel-B CTA
 
+// Fused one-pass plan: dual-pol, 2048..32768 channels, 8-tap PFB or direct.
+vspec_status build_fused_plan(vspec_plan *p) {
+    namespace F = vspec::fused;
+    namespace W = vspec::fusedw;
+    const int N = p->N;
+    const int N2 = F::kN2, N1 = N / N2;
+    const int logn1 = ilog2(N1);
+    const int PT = p->mode == VSPEC_PFB ? 8 : 1;
+    p->fused = true;
+    p->fused_w = (N1 == W::kN1);  // 32768 channels: warp-local FFT variant
+    p->logn1 = logn1;
+    p->N1 = N1;
+    p->N2 = N2;
+    p->cluster = N1 / F::kCols;
+    p->kernelR = (const void *)vspec::reduce_kernel<2>;
+    std::vector<int> rA, rB;
+    if (p->fused_w) {
+        p->kernelF = PT == 8 ? (const void *)W::fused_w_kernel<8> : (const void *)W::fused_w_kernel<1>;
+        p->smemF = W::smem_bytes();
+        for (int i = 0; i < 3; i++) rA.push_back(W::col_radix(i));
+        for (int i = 0; i < 3; i++) rB.push_back(W::row_radix(i));
+    } else {
+        p->kernelF = pick_kernel_fused(logn1, PT);
+        p->smemF = F::smem_bytes(logn1, PT);
+        for (int i = 0; i < F::kColPasses; i++) rA.push_back(F::col_radix(i));
+        for (int i = 0; i < F::row_passes(logn1); i++) rB.push_back(F::row_radix(logn1, i));
+    }
+    int twA_n = 0, twB_n = 0;
+    p->passA = make_passes(N2, rA, &twA_n);
+    p->passB = make_passes(N1, rB, &twB_n);
+
+    VSPEC_CUDA(cudaGetDevice(&p->device));
+    VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelF, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemF));
+    if (p->cluster > 8)
+        VSPEC_CUDA(cudaFuncSetAttribute(p->kernelF, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(p->cluster * std::max(1, p->num_sms / p->cluster));
+        cfg.blockDim = dim3(F::kThreads);
+        cfg.dynamicSmemBytes = p->smemF;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p->cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        VSPEC_CUDA(cudaOccupancyMaxActiveClusters(&ncl, p->kernelF, &cfg));
+        if (ncl < 1) {
+            g_last_error = "fused kernel: no cluster fits on this device";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        p->nclusters = ncl;
+    }
+
+    vspec_status st;
+    size_t tot = 0;
+    const int Lc = PT * N;
+    if ((st = dev_alloc((void **)&p->coef, sizeof(float) * (size_t)Lc, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twA, sizeof(float2) * (size_t)std::max(1, twA_n), &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twB, sizeof(float2) * (size_t)std::max(1, twB_n), &tot))) return st;
+    if ((st = dev_alloc((void **)&p->twZ, sizeof(float2) * (size_t)N, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->invA, sizeof(int) * (size_t)N2, &tot))) return st;
+    if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
+    if ((st = dev_alloc(&p->partial, (size_t)p->nclusters * N * sizeof(float4), &tot))) return st;
+    p->scratch_bytes = tot;
+    p->groups_b = p->nclusters;
+
+    const std::vector<int> kA = digit_reverse(N2, rA), kB = digit_reverse(N1, rB);
+    std::vector<int> invA(N2), invB(N1);
+    for (int pos = 0; pos < N2; pos++) invA[kA[pos]] = pos;
+    for (int pos = 0; pos < N1; pos++) invB[kB[pos]] = pos;
+    int *d_kA = nullptr;
+    if ((st = dev_alloc((void **)&d_kA, sizeof(int) * N2, &tot))) return st;
+    cudaError_t ce = cudaMemcpy(d_kA, kA.data(), sizeof(int) * N2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->invA, invA.data(), sizeof(int) * N2, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->invB, invB.data(), sizeof(int) * N1, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        vspec::gen_coef_kernel<<<(Lc + 255) / 256, 256>>>(p->coef, N, Lc, p->mode == VSPEC_PFB ? 1 : 0, p->window);
+        for (const Pass &ps : p->passA)
+            if (ps.m * (ps.r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256>>>(p->twA, ps);
+        for (const Pass &ps : p->passB)
+            if (ps.m * (ps.r - 1) > 0)
+                vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256>>>(p->twB, ps);
+        vspec::gen_twz_kernel<<<(N + 255) / 256, 256>>>(p->twZ, N, N1, N2, d_kA);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    }
+    cudaFree(d_kA);
+    if (ce != cudaSuccess) return cuda_fail(ce, "plan tables");
+    return VSPEC_OK;
+}
+
 vspec_status build_plan(vspec_plan *p) {
     const int N = p->N;
     const int e = ilog2(N);
     const bool pfb = p->mode == VSPEC_PFB;
+    if (!(p->flags & VSPEC_PLAN_TWO_KERNEL) && p->npol == 2 && N >= 2048 && N <= 32768 &&
+        (!pfb || p->P == 8))
+        return build_fused_plan(p);
     const int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
     const int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
     // largest column length kernel A can hold in registers (512 threads)
@@ -357,6 +499,11 @@ const char *vspec_last_error(void) { return g_last_error.c_str(); }
 
 vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
                                vspec_window window) {
+    return vspec_plan_create_ex(out, nchan, ntaps, npol, mode, window, 0u);
+}
+
+vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
+                                  vspec_window window, unsigned flags) {
     if (!out) return VSPEC_ERR_INVALID_ARG;
     *out = nullptr;
     if (!is_pow2(nchan) || nchan < 16 || nchan > (1 << 20)) return VSPEC_ERR_INVALID_ARG;
@@ -374,6 +521,12 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
     p->npol = npol;
     p->mode = mode;
     p->window = window;
+    if (flags & ~(unsigned)VSPEC_PLAN_TWO_KERNEL) {
+        delete p;
+        *out = nullptr;
+        return VSPEC_ERR_INVALID_ARG;
+    }
+    p->flags = flags;
     vspec_status st = build_plan(p);
     if (st != VSPEC_OK) {
         free_plan(p);
@@ -403,6 +556,52 @@ vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, f
     cudaStream_t st = (cudaStream_t)stream;
     vspec_plan *p = plan;
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+
+    if (p->fused_w) {
+        vspec::fusedw::Params wp;
+        wp.in = d_in;
+        wp.coef = p->coef;
+        wp.twA = p->twA;
+        wp.twB = p->twB;
+        wp.twZ = p->twZ;
+        wp.partial = reinterpret_cast<float4 *>(p->partial);
+        wp.nspectra = nspectra;
+        wp.nclusters = p->nclusters;
+        void *argsW[] = {&wp};
+        vspec_status r = launch(p, 3, nspectra, p->kernelF, dim3(p->cluster * p->nclusters),
+                                dim3(vspec::fusedw::kThreads), argsW, p->smemF, st, p->cluster);
+        if (r != VSPEC_OK) return r;
+        const void *part = p->partial;
+        int groups = p->nclusters, N = p->N, N1 = p->N1, N2 = p->N2;
+        const int *ia = p->invA, *ib = p->invB;
+        void *outp = d_accum;
+        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
+        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+    }
+    if (p->fused) {
+        vspec::fused::Params fp;
+        fp.in = d_in;
+        fp.coef = p->coef;
+        fp.twA = p->twA;
+        fp.twB = p->twB;
+        fp.twZ = p->twZ;
+        fp.partial = reinterpret_cast<float4 *>(p->partial);
+        fp.P = p->P;
+        fp.nspectra = nspectra;
+        fp.nclusters = p->nclusters;
+        for (int i = 0; i < vspec::fused::kColPasses; i++) fp.colp[i] = p->passA[i];
+        for (int i = 0; i < (int)p->passB.size(); i++) fp.rowp[i] = p->passB[i];
+        void *argsF[] = {&fp};
+        vspec_status r = launch(p, 3, nspectra, p->kernelF, dim3(p->cluster * p->nclusters),
+                                dim3(vspec::fused::kThreads), argsF, p->smemF, st, p->cluster);
+        if (r != VSPEC_OK) return r;
+        const void *part = p->partial;
+        int groups = p->nclusters, N = p->N, N1 = p->N1, N2 = p->N2;
+        const int *ia = p->invA, *ib = p->invB;
+        void *outp = d_accum;
+        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
+        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+    }
 
     VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->groups_b * p->N * accel, st));
 

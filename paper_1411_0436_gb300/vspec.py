@@ -26,6 +26,8 @@ ERR_CUDA = -4
 ERR_OOM = -5
 ERR_DEVICE_TIMEOUT = -6
 
+PLAN_TWO_KERNEL = 1  # force the general two-kernel path
+
 _lib = None
 
 
@@ -62,6 +64,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         vp, i, cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p
         lib.vspec_plan_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i]
         lib.vspec_plan_create.restype = i
+        lib.vspec_plan_create_ex.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, ctypes.c_uint]
+        lib.vspec_plan_create_ex.restype = i
         lib.vspec_plan_destroy.argtypes = [vp]
         lib.vspec_plan_destroy.restype = i
         lib.vspec_execute.argtypes = [vp, vp, i, vp, vp]
@@ -114,6 +118,15 @@ def vspec_plan_create(nchan: int, ntaps: int, npol: int, mode: int, window: int)
     st = load().vspec_plan_create(ctypes.byref(h), nchan, ntaps, npol, mode, window)
     if st != OK:
         raise VspecError(st, "vspec_plan_create")
+    return h.value
+
+
+def vspec_plan_create_ex(nchan: int, ntaps: int, npol: int, mode: int, window: int,
+                         flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = load().vspec_plan_create_ex(ctypes.byref(h), nchan, ntaps, npol, mode, window, flags)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_create_ex")
     return h.value
 
 
@@ -192,10 +205,11 @@ class Plan:
     """Owns one vspec plan; checks tensor shapes before calling the library."""
 
     def __init__(self, nchan: int, ntaps: int = 8, npol: int = 2, mode: int = PFB,
-                 window: int = WIN_HANN):
+                 window: int = WIN_HANN, flags: int = 0):
         self.nchan, self.ntaps, self.npol, self.mode, self.window = nchan, ntaps, npol, mode, window
         self.taps_used = 1 if mode == DIRECT else ntaps
-        self.handle = vspec_plan_create(nchan, ntaps, npol, mode, window)
+        self.handle = None
+        self.handle = vspec_plan_create_ex(nchan, ntaps, npol, mode, window, flags)
 
     @property
     def out_floats(self) -> int:

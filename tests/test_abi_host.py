@@ -41,6 +41,12 @@ def test_plan_create_rejects_bad_arguments(lib, args):
     assert h.value is None
 
 
+def test_plan_create_ex_rejects_unknown_flags(lib):
+    h = ctypes.c_void_p(123)
+    assert lib.vspec_plan_create_ex(ctypes.byref(h), 1024, 8, 2, 0, 1, 1 << 7) == vspec.ERR_INVALID_ARG
+    assert h.value is None
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.vspec_plan_create(None, 1024, 8, 2, 0, 1) == vspec.ERR_INVALID_ARG
     assert lib.vspec_execute(None, 16, 1, 16, None) == vspec.ERR_INVALID_ARG

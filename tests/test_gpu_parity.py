@@ -22,9 +22,9 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def run_gpu(bank: Bank, x: np.ndarray, repeat: int = 1) -> np.ndarray:
+def run_gpu(bank: Bank, x: np.ndarray, repeat: int = 1, flags: int = 0) -> np.ndarray:
     from paper_1411_0436_gb300.vspec import Plan
-    with Plan(bank.nchan, bank.ntaps, bank.npol, bank.mode, bank.window) as plan:
+    with Plan(bank.nchan, bank.ntaps, bank.npol, bank.mode, bank.window, flags) as plan:
         d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
         acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
         for _ in range(repeat):
@@ -56,6 +56,10 @@ SMALL = [
     (8192, 1, 2, DIRECT, WIN_HANN, 6),
     (16384, 8, 2, PFB, WIN_HANN, 10),
     (32768, 8, 2, PFB, WIN_HANN, 67),   # two scratch chunks, ragged second chunk
+    (32768, 8, 2, PFB, WIN_HANN, 1),    # fewer spectra than clusters
+    (32768, 1, 2, DIRECT, WIN_HANN, 23),
+    (2048, 1, 2, DIRECT, WIN_RECT, 40),
+    (16384, 8, 2, PFB, WIN_HAMMING, 300),
     (32768, 12, 2, PFB, WIN_HAMMING, 5),
     (65536, 8, 2, PFB, WIN_HANN, 4),
     (65536, 4, 1, PFB, WIN_HANN, 6),
@@ -66,15 +70,22 @@ SMALL = [
 ]
 
 
+def fused_applies(n, p, npol, mode):
+    """Sizes where a default plan takes the one-pass fused cluster path."""
+    return npol == 2 and 2048 <= n <= 32768 and (mode == DIRECT or p == 8)
+
+
 @pytest.mark.parametrize("cfg", SMALL, ids=lambda c: f"N{c[0]}_P{c[1]}_pol{c[2]}_m{c[3]}_w{c[4]}_S{c[5]}")
 def test_matches_oracle(oracle_mod, cfg):
+    from paper_1411_0436_gb300.vspec import PLAN_TWO_KERNEL
     n, p, npol, mode, win, s = cfg
     tones = (Tone(25.0, n * 0.3 + 0.4, (0, 1)),) if n >= 64 else ()
     bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3 if npol == 2 else 0.0, tones=tones)
     x = workloads.generate(bank, 1000 + n + p)
-    g = run_gpu(bank, x)
     o = run_oracle(oracle_mod, bank, x)
-    assert_close(g, o, what=str(cfg))
+    assert_close(run_gpu(bank, x), o, what=str(cfg))
+    if fused_applies(n, p, npol, mode):  # also the general path at the same size
+        assert_close(run_gpu(bank, x, flags=PLAN_TWO_KERNEL), o, what=f"{cfg} two-kernel")
 
 
 def test_impulse_is_bit_exact_for_every_int8_value():
