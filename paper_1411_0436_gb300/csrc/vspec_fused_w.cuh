@@ -40,7 +40,7 @@ constexpr int kR = 8;           // rows per CTA in the row phase
 constexpr int kCols = 16;       // columns per CTA in the column phase
 constexpr int kColStride = 129; // float4 per column (one pad element)
 constexpr int kExpStride = 16;  // float4 per exported row (columns XOR-swizzled)
-constexpr int kRowStride = 288; // float2 per (row, pol) unit: 256 + 256 / 8
+constexpr int kRowStride = 256; // float2 per (row, pol) unit (index-swizzled)
 
 // Radix plans (the plan builds its twiddle tables and digit-reversal maps
 // from the same lists).
@@ -60,10 +60,24 @@ struct Params {
     int nclusters;
 };
 
-__device__ __forceinline__ int rpad(int i) { return i + (i >> 3); }
-// Column-tile swizzle: keeps the stride-1, stride-4 and radix-8 access patterns
-// of the column DFT free of shared-memory bank conflicts.
-__device__ __forceinline__ int colf(int i) { return i ^ ((i >> 3) & 7); }
+// Swizzle of a row unit (256 float2): bits 4, 5, 6 of the index flip bits
+// 0..3 by 1, 10 and 4, keeping the gather, the three row passes and the
+// fused detection free of shared-memory bank conflicts.
+__device__ __forceinline__ int rpad(int i) {
+    return i ^ (((i >> 4) & 1) * 1) ^ (((i >> 5) & 1) * 10) ^ (((i >> 6) & 1) * 4);
+}
+// Swizzle of a column plane (128 float2 of one polarisation): bits 4, 5, 6 of
+// the index flip bits 0..3 by 1, 6 and 8, which keeps the three access
+// patterns of the column DFT (stride 1, the radix-8 pattern, stride 4) free
+// of shared-memory bank conflicts.
+__device__ __forceinline__ int cswz(int i) {
+    return i ^ (((i >> 4) & 1) * 1) ^ (((i >> 5) & 1) * 6) ^ (((i >> 6) & 1) * 8);
+}
+// int8 staging tile (one frame of the CTA's 128 x 16 samples, one 32-bit word
+// per dual-pol sample): row n2 keeps column c at word c ^ ((n2 >> 1) & 15), so
+// both the coalesced row-wise writes and the column-wise reads are free of
+// bank conflicts.
+__device__ __forceinline__ int rawslot(int n2, int c) { return n2 * 16 + (c ^ ((n2 >> 1) & 15)); }
 // Exported row pos keeps column c at slot c ^ ((pos >> 2) & 7).
 __device__ __forceinline__ int expf_slot(int pos, int c) { return pos * kExpStride + (c ^ ((pos >> 2) & 7)); }
 
@@ -71,54 +85,69 @@ __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); 
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 __host__ __device__ constexpr size_t smem_bytes() {
-    return (size_t)kCols * kColStride * 16 +        // column tile
+    return (size_t)kN2 * kCols * 4 +                // int8 staging tile
+           (size_t)2 * kCols * kN2 * 8 +            // column planes
            (size_t)2 * kN2 * kExpStride * 16 +      // exported rows, double-buffered
            (size_t)2 * kR * kRowStride * 8 +         // row units
            (size_t)8 * kThreads * 16 +               // coefficients
            (size_t)(kColTwN + kRowTwN) * 8;          // twiddles
 }
 
-// 128-point column DFT of column `c` (this warp), results exported by position.
-__device__ __forceinline__ void column_dft(float4 *col, float4 *exp, const float2 *twc, int c, int lane) {
+// 128-point column DFT of column `c` (this warp) from its pre-filtered rows
+// lane + 32 i held in registers; results exported by position.
+__device__ __forceinline__ void column_dft(float4 (&v)[4], float2 *px, float2 *py, float4 *exp,
+                                           const float2 (&tw1)[3], const float2 *twc, int c, int lane) {
     // A1: radix 4 over n2 = lane + 32 i, twiddle W_128^(lane q)
-    {
-        float4 v[4];
+    Dft<4>::run(v);
 #pragma unroll
-        for (int i = 0; i < 4; i++) v[i] = col[colf(lane + 32 * i)];
-        Dft<4>::run(v);
+    for (int q = 1; q < 4; q++) v[q] = cmul(v[q], tw1[q - 1]);
 #pragma unroll
-        for (int q = 1; q < 4; q++) v[q] = cmul(v[q], twc[kColTw0 + lane * 3 + q - 1]);
-#pragma unroll
-        for (int q = 0; q < 4; q++) col[colf(lane + 32 * q)] = v[q];
+    for (int q = 0; q < 4; q++) {
+        px[cswz(lane + 32 * q)] = make_float2(v[q].x, v[q].y);
+        py[cswz(lane + 32 * q)] = make_float2(v[q].z, v[q].w);
     }
     __syncwarp();
     // A2: radix 8 inside each 32-block, one polarisation per half-warp
     {
-        float2 *col2 = reinterpret_cast<float2 *>(col);
-        const int pol = lane >> 4, b = lane & 15, qb = b >> 2, j = b & 3;
-        float2 v[8];
+        float2 *pl = (lane >> 4) ? py : px;
+        const int b = lane & 15, qb = b >> 2, j = b & 3;
+        float2 w[8];
 #pragma unroll
-        for (int m = 0; m < 8; m++) v[m] = col2[colf(qb * 32 + j + 4 * m) * 2 + pol];
-        Dft<8>::run(v);
+        for (int m = 0; m < 8; m++) w[m] = pl[cswz(qb * 32 + j + 4 * m)];
+        Dft<8>::run(w);
 #pragma unroll
-        for (int m = 1; m < 8; m++) v[m] = cmul(v[m], twc[kColTw1 + j * 7 + m - 1]);
+        for (int m = 1; m < 8; m++) w[m] = cmul(w[m], twc[kColTw1 + j * 7 + m - 1]);
 #pragma unroll
-        for (int m = 0; m < 8; m++) col2[colf(qb * 32 + j + 4 * m) * 2 + pol] = v[m];
+        for (int m = 0; m < 8; m++) pl[cswz(qb * 32 + j + 4 * m)] = w[m];
     }
     __syncwarp();
     // A3: radix 4 on contiguous blocks, export position 4 lane + q
     {
-        float4 v[4];
+        float4 u[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) v[q] = col[colf(4 * lane + q)];
-        Dft<4>::run(v);
+        for (int q = 0; q < 4; q++) {
+            const float2 a = px[cswz(4 * lane + q)], b = py[cswz(4 * lane + q)];
+            u[q] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        Dft<4>::run(u);
 #pragma unroll
-        for (int q = 0; q < 4; q++) exp[expf_slot(4 * lane + q, c)] = v[q];
+        for (int q = 0; q < 4; q++) exp[expf_slot(4 * lane + q, c)] = u[q];
     }
 }
 
-// 256-point row DFT of one (row, pol) unit, in place, outputs by position.
-__device__ __forceinline__ void row_dft(float2 *u, const float2 *twr, int lane) {
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
+
+// Row DFTs of the CTA's 8 rows (warp 2 r + p: row r, polarisation p), fused
+// with detection and accumulation. The first two passes run on the warp's own
+// unit; the last radix-8 pass takes blocks 16 p .. 16 p + 15 of row r for
+// both polarisations (lanes 0-15: X, lanes 16-31: Y), so after one shuffle
+// each lane holds X and Y for four channels.
+__device__ __forceinline__ void rows_detect(float2 *rowbuf, const float2 *twr, const float2 (&tw2)[3],
+                                            int warp, int lane, float4 (&acc)[4]) {
+    const int r = warp >> 1, p = warp & 1;
+    float2 *u = rowbuf + warp * kRowStride;
     {
         float2 v[8];
 #pragma unroll
@@ -138,37 +167,26 @@ __device__ __forceinline__ void row_dft(float2 *u, const float2 *twr, int lane) 
         for (int m = 0; m < 4; m++) v[m] = u[rpad(qb * 32 + j + 8 * m)];
         Dft<4>::run(v);
 #pragma unroll
-        for (int m = 1; m < 4; m++) v[m] = cmul(v[m], twr[kRowTw1 + j * 3 + m - 1]);
+        for (int m = 1; m < 4; m++) v[m] = cmul(v[m], tw2[m - 1]);  // W_32^(j m), j = lane & 7
 #pragma unroll
         for (int m = 0; m < 4; m++) u[rpad(qb * 32 + j + 8 * m)] = v[m];
     }
-    __syncwarp();
-    {
-        float2 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) v[q] = u[rpad(8 * lane + q)];
-        Dft<8>::run(v);
-#pragma unroll
-        for (int q = 0; q < 8; q++) u[rpad(8 * lane + q)] = v[q];
-    }
-}
-
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
-}
-
-// Row DFTs of the CTA's 8 rows, then detection and accumulation.
-__device__ __forceinline__ void rows_detect(float2 *rowbuf, const float2 *twr, int warp, int lane,
-                                            float4 (&acc)[4]) {
-    const int r = warp >> 1, p = warp & 1;
-    row_dft(rowbuf + warp * kRowStride, twr, lane);
     named_barrier(1 + r, 64);
-    const float2 *ux = rowbuf + (2 * r) * kRowStride, *uy = rowbuf + (2 * r + 1) * kRowStride;
+    const int half = lane >> 4, b = 16 * p + (lane & 15);
+    const float2 *src = rowbuf + (2 * r + half) * kRowStride;
+    float2 v[8];
 #pragma unroll
-    for (int qq = 0; qq < 4; qq++) {
-        const int pos = 8 * lane + 4 * p + qq;
-        const float2 x = ux[rpad(pos)], y = uy[rpad(pos)];
-        acc_add<2>(acc[qq], make_float4(x.x, x.y, y.x, y.y));
+    for (int q = 0; q < 8; q++) v[q] = src[rpad(8 * b + q)];
+    Dft<8>::run(v);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float2 send = half ? v[k] : v[4 + k];
+        float2 recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+        const float2 x = half ? recv : v[k];
+        const float2 y = half ? v[4 + k] : recv;
+        acc_add<2>(acc[k], make_float4(x.x, x.y, y.x, y.y));
     }
 }
 
@@ -176,8 +194,9 @@ __device__ __forceinline__ void rows_detect(float2 *rowbuf, const float2 *twr, i
 template <int PT>
 __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_constant__ Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *colbuf = reinterpret_cast<float4 *>(smem_raw);                      // [16][129]
-    float4 *expbuf = colbuf + kCols * kColStride;                               // [2][128][17]
+    uint32_t *raw = reinterpret_cast<uint32_t *>(smem_raw);                     // [128][16] words
+    float2 *planes = reinterpret_cast<float2 *>(raw + kN2 * kCols);             // [2 pol][16][128]
+    float4 *expbuf = reinterpret_cast<float4 *>(planes + 2 * kCols * kN2);      // [2][128][16]
     float2 *rowbuf = reinterpret_cast<float2 *>(expbuf + 2 * kN2 * kExpStride); // [16][288]
     float4 *coefs = reinterpret_cast<float4 *>(rowbuf + 2 * kR * kRowStride);   // [8][512]
     float2 *twc = reinterpret_cast<float2 *>(coefs + 8 * kThreads);             // column twiddles
@@ -192,23 +211,40 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
     const int s_beg = (int)((long long)p.nspectra * cl / p.nclusters);
     const int s_end = (int)((long long)p.nspectra * (cl + 1) / p.nclusters);
 
-    // column-phase samples of this thread: column c, rows n2b + 32 i
-    const int c = tid & (kCols - 1), n2b = tid >> 4;
-    const long long n0 = (long long)j * kCols + c + (long long)kN1 * n2b;
+    // Loading set (coalesced): column cl, rows n2b + 32 i. Compute set (the
+    // pre-filter, its delay line and the column DFT): column `warp`, rows
+    // lane + 32 i.
+    const int cl_ = tid & (kCols - 1), n2b = tid >> 4;
+    const long long n0 = (long long)j * kCols + cl_ + (long long)kN1 * n2b;
+    const long long m0 = (long long)j * kCols + warp + (long long)kN1 * lane;
     const unsigned int *in4 = reinterpret_cast<const unsigned int *>(p.in);
     auto load_frame = [&](long long f, uint32_t (&w)[4]) {
 #pragma unroll
         for (int i = 0; i < 4; i++) w[i] = __ldg(in4 + f * kN + n0 + (long long)kN1 * 32 * i);
     };
+    auto stage = [&](const uint32_t (&w)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) raw[rawslot(n2b + 32 * i, cl_)] = w[i];
+    };
+    auto unstage = [&](uint32_t (&w)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) w[i] = raw[rawslot(lane + 32 * i, warp)];
+    };
 
 #pragma unroll
     for (int t = 0; t < PT; t++) {
         float4 h;
-        h.x = __ldg(p.coef + (size_t)t * kN + n0);
-        h.y = __ldg(p.coef + (size_t)t * kN + n0 + kN1 * 32);
-        h.z = __ldg(p.coef + (size_t)t * kN + n0 + kN1 * 64);
-        h.w = __ldg(p.coef + (size_t)t * kN + n0 + kN1 * 96);
+        h.x = __ldg(p.coef + (size_t)t * kN + m0);
+        h.y = __ldg(p.coef + (size_t)t * kN + m0 + kN1 * 32);
+        h.z = __ldg(p.coef + (size_t)t * kN + m0 + kN1 * 64);
+        h.w = __ldg(p.coef + (size_t)t * kN + m0 + kN1 * 96);
         coefs[t * kThreads + tid] = h;
+    }
+    float2 tw1[3], tw2[3];
+#pragma unroll
+    for (int q = 1; q < 4; q++) {
+        tw1[q - 1] = __ldg(p.twA + kColTw0 + lane * 3 + q - 1);
+        tw2[q - 1] = __ldg(p.twB + kRowTw1 + (lane & 7) * 3 + q - 1);
     }
     for (int e = tid; e < kColTwN; e += kThreads) twc[e] = __ldg(p.twA + e);
     for (int e = tid; e < kRowTwN; e += kThreads) twr[e] = __ldg(p.twB + e);
@@ -236,11 +272,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
     for (int q = 0; q < 4; q++) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     if (s_beg < s_end) {
+        __syncthreads();
         if constexpr (PT > 1) {
             for (int t = 0; t < PT - 1; t++) {
                 const long long f = s_beg + t;
                 uint32_t w[4];
                 load_frame(f, w);
+                stage(w);
+                __syncthreads();
+                unstage(w);
+                __syncthreads();
                 float v[16];
                 unpack4(w, v);
                 tmem_st16(taddr + 16u * (uint32_t)(f & 7), v);
@@ -249,15 +290,18 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
         }
         uint32_t nxt[4];
         load_frame((long long)s_beg + PT - 1, nxt);
-        __syncthreads();
 
         for (int s = s_beg; s < s_end; s++) {
             float4 *exp = expbuf + (s & 1) * kN2 * kExpStride;
-            // ---- pre-filter (§4, PFB)
+            stage(nxt);
+            __syncthreads();
+            // ---- pre-filter (§4, PFB) of the compute set
             float y[16];
             {
+                uint32_t w[4];
+                unstage(w);
                 float v[16];
-                unpack4(nxt, v);
+                unpack4(w, v);
                 const float4 h = coefs[(PT - 1) * kThreads + tid];
                 const float hh[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
@@ -284,16 +328,17 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
                 }
                 tmem_st_wait();
             }
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-                colbuf[c * kColStride + colf(n2b + 32 * i)] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
-            __syncthreads();
             // ---- column DFT: warp w owns column w
-            column_dft(colbuf + warp * kColStride, exp, twc, warp, lane);
+            {
+                float4 v4[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) v4[i] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+                column_dft(v4, planes + warp * kN2, planes + (kCols + warp) * kN2, exp, tw1, twc, warp, lane);
+            }
             // ---- exchange: the cluster barrier publishes the exported rows
             cluster.barrier_arrive();
             if (s + 1 < s_end) load_frame((long long)s + PT, nxt);
-            if (s > s_beg) rows_detect(rowbuf, twr, warp, lane, acc);  // spectrum s - 1
+            if (s > s_beg) rows_detect(rowbuf, twr, tw2, warp, lane, acc);  // spectrum s - 1
             __syncthreads();
             cluster.barrier_wait();
 #pragma unroll
@@ -307,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
             }
         }
         __syncthreads();
-        rows_detect(rowbuf, twr, warp, lane, acc);  // last spectrum
+        rows_detect(rowbuf, twr, tw2, warp, lane, acc);  // last spectrum
     }
     cluster.sync();
 
@@ -318,9 +363,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_w_kernel(const __grid_const
         if (warp == 0) tmem_dealloc(tmem_base_slot, 512);
     }
 
-    // accumulators -> partial[cl][pos][posB], pos = 8 j + r, posB = 8 lane + 4 p + qq
+    // accumulators -> partial[cl][pos][posB], pos = 8 j + r,
+    // posB = 8 (16 pp + lane % 16) + 4 (lane / 16) + k
     const int r = warp >> 1, pp = warp & 1;
-    float4 *dst = p.partial + (size_t)cl * kN + (size_t)(kR * j + r) * kN1 + 8 * lane + 4 * pp;
+    float4 *dst = p.partial + (size_t)cl * kN + (size_t)(kR * j + r) * kN1 +
+                  8 * (16 * pp + (lane & 15)) + 4 * (lane >> 4);
 #pragma unroll
     for (int q = 0; q < 4; q++) dst[q] = acc[q];
 }
