@@ -117,6 +117,28 @@ VSPEC_API vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int n
                            float *d_accum, void *stream);
 
 /*
+ * The whole loop of §4 from host memory: copy the time series to the device,
+ * pre-filter, FFT, detect and accumulate, and copy the output to the host,
+ * with the copies overlapped with the compute through CUDA streams (the
+ * pipelining §6 proposes).
+ *   h_in   host int8, layout and size as d_in of vspec_execute. Pinned
+ *          memory (cudaHostAlloc / cudaHostRegister) lets copies overlap
+ *          compute; pageable memory works but serialises.
+ *   h_out  host float[nchan * 4] (npol == 2) or float[nchan]: overwritten
+ *          with the accumulated spectra of these nspectra spectra.
+ * The spectra are processed in chunks of about 32 MiB of input: a plan-owned
+ * copy stream fills one of two device staging buffers while a plan-owned
+ * compute stream channelizes the other. All work starts after the work
+ * already queued on `stream`, and `stream` waits for the final copy, so the
+ * caller synchronises `stream` before reading h_out. The first call on a plan
+ * allocates the staging buffers (two chunks of input plus one accumulator)
+ * and creates the streams. Calls on one plan must be serialised.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspectra,
+                                          float *h_out, void *stream);
+
+/*
  * Dump the accumulator (§4, "copy output to host") and clear it.
  *   h_out  host buffer of nchan * (npol == 2 ? 4 : 1) floats, or NULL to clear
  *          only. Pinned host memory makes the copy asynchronous; with pageable
@@ -185,6 +207,54 @@ VSPEC_API vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int r
 VSPEC_API vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int ntaps, int npol,
                                              vspec_mode mode, vspec_window window, int nspectra,
                                              float *d_accum, void *stream);
+
+/*
+ * Batches: many banks (beams or sub-bands, §3 runs one pipeline per beam) of
+ * possibly different sizes and modes, channelized by one CUDA-graph launch.
+ * A batch owns one plan per bank. The first vspec_batch_execute (and any
+ * later call whose pointers or spectrum counts differ from the previous one)
+ * records every bank's kernels into a CUDA graph, one forked stream branch
+ * per bank so that banks run concurrently; other calls replay that graph with
+ * a single launch on `stream`. Each bank follows the conventions of
+ * vspec_execute for its own input and accumulator. Do not call
+ * vspec_batch_execute while `stream` is being captured.
+ */
+typedef struct {
+    int nchan;            /* as vspec_plan_create */
+    int ntaps;
+    int npol;
+    vspec_mode mode;
+    vspec_window window;
+} vspec_bank;
+
+typedef struct vspec_batch vspec_batch;
+
+/* Create a batch of nbanks (1..256) banks. Errors as vspec_plan_create. */
+VSPEC_API vspec_status vspec_batch_create(vspec_batch **out, int nbanks, const vspec_bank *banks);
+
+/* Release a batch and its plans. NULL is accepted. */
+VSPEC_API vspec_status vspec_batch_destroy(vspec_batch *batch);
+
+/*
+ * Channelize every bank: d_in[i], nspectra[i], d_accum[i] are bank i's
+ * arguments of vspec_execute (host arrays of nbanks entries; the pointers they
+ * hold are device pointers). Asynchronous on `stream`.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_ALIGNMENT, VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *const *d_in,
+                                           const int *nspectra, float *const *d_accum, void *stream);
+
+/*
+ * Autotuner: for each bank, time `reps` executions of every applicable kernel
+ * path (the one-pass fused path and the two-kernel path) on the given
+ * arguments and keep the faster plan. Clears every d_accum[i] afterwards and
+ * synchronises `stream`. vspec_batch_bank_flags reports the VSPEC_PLAN_*
+ * flags of the plan chosen for bank `bank`.
+ */
+VSPEC_API vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
+                                            const int *nspectra, float *const *d_accum,
+                                            void *stream, int reps);
+VSPEC_API vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags);
 
 /* Static, human-readable text for a status code. */
 VSPEC_API const char *vspec_status_string(vspec_status status);

@@ -38,6 +38,18 @@ vspec_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// The dynamic shared-memory cap is a property of the kernel function, shared
+// by every plan that launches it: only ever raise it, never lower it.
+std::mutex g_smem_attr_mu;
+cudaError_t raise_smem_cap(const void *fn, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_smem_attr_mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 int ilog2(long long v) {
     int e = 0;
     while ((1LL << e) < v) e++;
@@ -124,6 +136,14 @@ struct vspec_plan {
     bool profiling = false;
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> event_pool;
+    // host-input pipeline (vspec_execute_host), created on first use
+    bool host_ready = false;
+    cudaStream_t copy_st = nullptr, comp_st = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    int8_t *stage[2] = {nullptr, nullptr};
+    float *hacc = nullptr;
+    int stage_spectra = 0;
 };
 
 namespace {
@@ -227,6 +247,18 @@ void free_plan(vspec_plan *p) {
     if (!p) return;
     release_records(p);
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    if (p->host_ready) {
+        cudaStreamDestroy(p->copy_st);
+        cudaStreamDestroy(p->comp_st);
+        cudaEventDestroy(p->ev_start);
+        cudaEventDestroy(p->ev_done);
+        for (int b = 0; b < 2; b++) {
+            cudaEventDestroy(p->ev_copied[b]);
+            cudaEventDestroy(p->ev_used[b]);
+            cudaFree(p->stage[b]);
+        }
+        cudaFree(p->hacc);
+    }
     cudaFree(p->coef);
     cudaFree(p->twA);
     cudaFree(p->twB);
@@ -288,7 +320,7 @@ vspec_status build_fused_plan(vspec_plan *p) {
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelF, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemF));
+    VSPEC_CUDA(raise_smem_cap(p->kernelF, p->smemF));
     if (p->cluster > 8)
         VSPEC_CUDA(cudaFuncSetAttribute(p->kernelF, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     {
@@ -419,8 +451,8 @@ vspec_status build_plan(vspec_plan *p) {
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
-    VSPEC_CUDA(cudaFuncSetAttribute(p->kernelB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    VSPEC_CUDA(raise_smem_cap(p->kernelA, p->smemA));
+    VSPEC_CUDA(raise_smem_cap(p->kernelB, p->smemB));
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occA, p->kernelA, p->TA, p->smemA));
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occB, p->kernelB, p->TB, p->smemB));
     if (p->occA < 1 || p->occB < 1) {
@@ -695,6 +727,66 @@ vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset, cons
     return VSPEC_OK;
 }
 
+// Spectra per chunk of the host-input pipeline: about 32 MiB of input per
+// staging buffer (at least 16 spectra), so copies and compute overlap.
+static int host_chunk_spectra(const vspec_plan *p) {
+    const size_t per = (size_t)p->N * p->npol * 2;
+    return (int)std::max<size_t>(16, (32u << 20) / per);
+}
+
+vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspectra, float *h_out,
+                                void *stream) {
+    if (!plan || !h_in || !h_out || nspectra < 0) return VSPEC_ERR_INVALID_ARG;
+    vspec_plan *p = plan;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Peff = p->mode == VSPEC_PFB ? p->P : 1;
+    const size_t frame = (size_t)p->N * p->npol * 2;
+    const size_t out_bytes = (size_t)p->N * (p->npol == 2 ? 4 : 1) * sizeof(float);
+    if (!p->host_ready) {
+        p->stage_spectra = host_chunk_spectra(p);
+        const size_t sbytes = (size_t)(p->stage_spectra + Peff - 1) * frame;
+        size_t tot = 0;
+        vspec_status r;
+        for (int b = 0; b < 2; b++)
+            if ((r = dev_alloc((void **)&p->stage[b], sbytes, &tot))) return r;
+        if ((r = dev_alloc((void **)&p->hacc, out_bytes, &tot))) return r;
+        VSPEC_CUDA(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking));
+        VSPEC_CUDA(cudaStreamCreateWithFlags(&p->comp_st, cudaStreamNonBlocking));
+        VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+        VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming));
+        for (int b = 0; b < 2; b++) {
+            VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_copied[b], cudaEventDisableTiming));
+            VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_used[b], cudaEventDisableTiming));
+        }
+        p->scratch_bytes += tot;
+        p->host_ready = true;
+    }
+    // both internal streams start after the work already queued on `stream`
+    VSPEC_CUDA(cudaEventRecord(p->ev_start, st));
+    VSPEC_CUDA(cudaStreamWaitEvent(p->copy_st, p->ev_start, 0));
+    VSPEC_CUDA(cudaStreamWaitEvent(p->comp_st, p->ev_start, 0));
+    VSPEC_CUDA(cudaMemsetAsync(p->hacc, 0, out_bytes, p->comp_st));
+    const int chunk = p->stage_spectra;
+    int k = 0;
+    for (int s0 = 0; s0 < nspectra; s0 += chunk, k++) {
+        const int cnt = std::min(chunk, nspectra - s0);
+        const int b = k & 1;
+        // the buffer is free once the compute that read it two chunks ago is done
+        if (k >= 2) VSPEC_CUDA(cudaStreamWaitEvent(p->copy_st, p->ev_used[b], 0));
+        VSPEC_CUDA(cudaMemcpyAsync(p->stage[b], h_in + (size_t)s0 * frame, (size_t)(cnt + Peff - 1) * frame,
+                                   cudaMemcpyHostToDevice, p->copy_st));
+        VSPEC_CUDA(cudaEventRecord(p->ev_copied[b], p->copy_st));
+        VSPEC_CUDA(cudaStreamWaitEvent(p->comp_st, p->ev_copied[b], 0));
+        vspec_status r = vspec_execute(p, p->stage[b], cnt, p->hacc, (void *)p->comp_st);
+        if (r != VSPEC_OK) return r;
+        VSPEC_CUDA(cudaEventRecord(p->ev_used[b], p->comp_st));
+    }
+    VSPEC_CUDA(cudaMemcpyAsync(h_out, p->hacc, out_bytes, cudaMemcpyDeviceToHost, p->comp_st));
+    VSPEC_CUDA(cudaEventRecord(p->ev_done, p->comp_st));
+    VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
+    return VSPEC_OK;
+}
+
 vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *stream) {
     if (!plan || !d_accum) return VSPEC_ERR_INVALID_ARG;
     if (!aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
@@ -843,8 +935,8 @@ vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
     const size_t accel = c->npol == 2 ? sizeof(float4) : sizeof(float);
     c->smemA = (size_t)PT * N2 * C * elem;
     c->smemB = (size_t)c->RB * (N1 + (N1 >> 4)) * elem + (size_t)c->RB * N1 * accel;
-    VSPEC_CUDA(cudaFuncSetAttribute(c->kA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smemA));
-    VSPEC_CUDA(cudaFuncSetAttribute(c->kB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smemB));
+    VSPEC_CUDA(raise_smem_cap(c->kA, c->smemA));
+    VSPEC_CUDA(raise_smem_cap(c->kB, c->smemB));
     int occB = 1;
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occA, c->kA, c->TA, c->smemA));
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, c->kB, c->TB, c->smemB));

@@ -1,0 +1,219 @@
+// vspec_batch.cu — many banks (beams, sub-bands) channelized by one CUDA-graph launch.
+//
+// VEGAS runs one spectrometer pipeline per beam (§3 of arXiv 1411.0436), and
+// the per-invocation launch and copy overheads dominate at small FFT lengths
+// (§5). A batch owns one plan per bank; vspec_batch_execute records every
+// bank's kernels into one CUDA graph, one forked stream branch per bank so
+// that banks of different sizes run concurrently, and replays it with a
+// single graph launch. Built only on the public C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vspec.h"
+
+struct vspec_batch {
+    int nbanks = 0;
+    std::vector<vspec_bank> desc;
+    std::vector<vspec_plan *> plans;
+    std::vector<unsigned> flags;
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> joined;
+    cudaStream_t capture = nullptr;
+    cudaEvent_t forked = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // arguments the graph was captured with
+    std::vector<const int8_t *> g_in;
+    std::vector<int> g_ns;
+    std::vector<float *> g_acc;
+};
+
+namespace {
+
+void destroy_batch(vspec_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (vspec_plan *p : b->plans) vspec_plan_destroy(p);
+    for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->joined) cudaEventDestroy(e);
+    if (b->forked) cudaEventDestroy(b->forked);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+}
+
+vspec_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return VSPEC_OK;
+    return e == cudaErrorMemoryAllocation ? VSPEC_ERR_OOM : VSPEC_ERR_CUDA;
+}
+
+// Record all banks into a graph: fork from `capture` to one branch per bank,
+// vspec_execute on each branch, join back.
+vspec_status capture_graph(vspec_batch *b, const int8_t *const *d_in, const int *nspectra,
+                           float *const *d_accum) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return VSPEC_ERR_CUDA;
+    vspec_status st = VSPEC_OK;
+    e = cudaEventRecord(b->forked, b->capture);
+    for (int i = 0; i < b->nbanks && e == cudaSuccess && st == VSPEC_OK; i++) {
+        e = cudaStreamWaitEvent(b->branch[i], b->forked, 0);
+        if (e != cudaSuccess) break;
+        st = vspec_execute(b->plans[i], d_in[i], nspectra[i], d_accum[i], (void *)b->branch[i]);
+        if (st != VSPEC_OK) break;
+        e = cudaEventRecord(b->joined[i], b->branch[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->joined[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
+    if (st != VSPEC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return VSPEC_ERR_CUDA;
+    }
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return VSPEC_ERR_CUDA;
+    b->g_in.assign(d_in, d_in + b->nbanks);
+    b->g_ns.assign(nspectra, nspectra + b->nbanks);
+    b->g_acc.assign(d_accum, d_accum + b->nbanks);
+    return VSPEC_OK;
+}
+
+bool same_args(const vspec_batch *b, const int8_t *const *d_in, const int *nspectra,
+               float *const *d_accum) {
+    if (!b->exec) return false;
+    for (int i = 0; i < b->nbanks; i++)
+        if (b->g_in[i] != d_in[i] || b->g_ns[i] != nspectra[i] || b->g_acc[i] != d_accum[i]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+vspec_status vspec_batch_create(vspec_batch **out, int nbanks, const vspec_bank *banks) {
+    if (!out) return VSPEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nbanks < 1 || nbanks > 256 || !banks) return VSPEC_ERR_INVALID_ARG;
+    vspec_batch *b = new (std::nothrow) vspec_batch();
+    if (!b) return VSPEC_ERR_OOM;
+    b->nbanks = nbanks;
+    b->desc.assign(banks, banks + nbanks);
+    b->flags.assign(nbanks, 0u);
+    for (int i = 0; i < nbanks; i++) {
+        vspec_plan *p = nullptr;
+        const vspec_bank &d = banks[i];
+        vspec_status st = vspec_plan_create(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window);
+        if (st != VSPEC_OK) {
+            destroy_batch(b);
+            return st;
+        }
+        b->plans.push_back(p);
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            if (s) cudaStreamDestroy(s);
+            destroy_batch(b);
+            return VSPEC_ERR_CUDA;
+        }
+        b->branch.push_back(s);
+        b->joined.push_back(e);
+    }
+    if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) != cudaSuccess) {
+        destroy_batch(b);
+        return VSPEC_ERR_CUDA;
+    }
+    *out = b;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_batch_destroy(vspec_batch *batch) {
+    destroy_batch(batch);
+    return VSPEC_OK;
+}
+
+vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *const *d_in, const int *nspectra,
+                                 float *const *d_accum, void *stream) {
+    if (!batch || !d_in || !nspectra || !d_accum) return VSPEC_ERR_INVALID_ARG;
+    for (int i = 0; i < batch->nbanks; i++) {
+        if (!d_in[i] || !d_accum[i] || nspectra[i] < 0) return VSPEC_ERR_INVALID_ARG;
+        if (((uintptr_t)d_in[i] & 15u) || ((uintptr_t)d_accum[i] & 15u)) return VSPEC_ERR_ALIGNMENT;
+    }
+    if (!same_args(batch, d_in, nspectra, d_accum)) {
+        vspec_status st = capture_graph(batch, d_in, nspectra, d_accum);
+        if (st != VSPEC_OK) return st;
+    }
+    return cuda_status(cudaGraphLaunch(batch->exec, (cudaStream_t)stream));
+}
+
+vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in, const int *nspectra,
+                                  float *const *d_accum, void *stream, int reps) {
+    if (!batch || !d_in || !nspectra || !d_accum || reps < 1) return VSPEC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) return VSPEC_ERR_CUDA;
+    vspec_status result = VSPEC_OK;
+    for (int i = 0; i < batch->nbanks && result == VSPEC_OK; i++) {
+        const vspec_bank &d = batch->desc[i];
+        const unsigned cand[2] = {0u, VSPEC_PLAN_TWO_KERNEL};
+        float best = 1e30f;
+        vspec_plan *best_plan = nullptr;
+        unsigned best_flags = 0;
+        for (unsigned f : cand) {
+            vspec_plan *p = nullptr;
+            if (vspec_plan_create_ex(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window, f) != VSPEC_OK) continue;
+            vspec_status s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);  // warm-up
+            cudaEventRecord(t0, st);
+            for (int r = 0; r < reps && s == VSPEC_OK; r++)
+                s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);
+            cudaEventRecord(t1, st);
+            float ms = 0.f;
+            if (s == VSPEC_OK && cudaEventSynchronize(t1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best) {
+                if (best_plan) vspec_plan_destroy(best_plan);
+                best_plan = p;
+                best = ms;
+                best_flags = f;
+            } else {
+                cudaStreamSynchronize(st);
+                vspec_plan_destroy(p);
+            }
+        }
+        if (!best_plan) {
+            result = VSPEC_ERR_CUDA;
+            break;
+        }
+        cudaStreamSynchronize(st);
+        vspec_plan_destroy(batch->plans[i]);
+        batch->plans[i] = best_plan;
+        batch->flags[i] = best_flags;
+        const size_t bytes = (size_t)d.nchan * (d.npol == 2 ? 4 : 1) * sizeof(float);
+        if (cudaMemsetAsync(d_accum[i], 0, bytes, st) != cudaSuccess) result = VSPEC_ERR_CUDA;
+    }
+    if (batch->exec) {
+        cudaGraphExecDestroy(batch->exec);
+        batch->exec = nullptr;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return result;
+}
+
+vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags) {
+    if (!batch || bank < 0 || bank >= batch->nbanks || !flags) return VSPEC_ERR_INVALID_ARG;
+    *flags = batch->flags[bank];
+    return VSPEC_OK;
+}
+
+}  // extern "C"

@@ -79,6 +79,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_kernel_stats.argtypes = [vp, i, i, ctypes.POINTER(cp), ctypes.POINTER(ctypes.c_longlong),
                                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
         lib.vspec_plan_kernel_stats.restype = i
+        lib.vspec_batch_create.argtypes = [ctypes.POINTER(vp), i, vp]
+        lib.vspec_batch_create.restype = i
+        lib.vspec_batch_destroy.argtypes = [vp]
+        lib.vspec_batch_destroy.restype = i
+        lib.vspec_batch_execute.argtypes = [vp, vp, vp, vp, vp]
+        lib.vspec_batch_execute.restype = i
+        lib.vspec_batch_autotune.argtypes = [vp, vp, vp, vp, vp, i]
+        lib.vspec_batch_autotune.restype = i
+        lib.vspec_batch_bank_flags.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint)]
+        lib.vspec_batch_bank_flags.restype = i
+        lib.vspec_execute_host.argtypes = [vp, vp, i, vp, vp]
+        lib.vspec_execute_host.restype = i
         lib.vspec_execute_noalloc.argtypes = [vp, i, i, i, i, i, i, vp, vp]
         lib.vspec_execute_noalloc.restype = i
         lib.vspec_status_string.argtypes = [i]
@@ -140,6 +152,12 @@ def vspec_execute(plan: int, d_in, nspectra: int, d_accum, stream=None) -> None:
     st = load().vspec_execute(plan, _addr(d_in), nspectra, _addr(d_accum), _stream(stream))
     if st != OK:
         raise VspecError(st, "vspec_execute")
+
+
+def vspec_execute_host(plan: int, h_in, nspectra: int, h_out, stream=None) -> None:
+    st = load().vspec_execute_host(plan, _addr(h_in), nspectra, _addr(h_out), _stream(stream))
+    if st != OK:
+        raise VspecError(st, "vspec_execute_host")
 
 
 def vspec_dump(plan: int, d_accum, h_out=None, stream=None) -> None:
@@ -229,6 +247,10 @@ class Plan:
                 raise ValueError("d_accum must be a contiguous CUDA float tensor of nchan*(4|1) floats")
         vspec_execute(self.handle, d_in, nspectra, d_accum, stream)
 
+    def execute_host(self, h_in, nspectra: int, h_out, stream=None) -> None:
+        """Host input -> host output with overlapped copies (see vspec_execute_host)."""
+        vspec_execute_host(self.handle, h_in, nspectra, h_out, stream)
+
     def dump(self, d_accum, h_out=None, stream=None) -> None:
         vspec_dump(self.handle, d_accum, h_out, stream)
 
@@ -244,6 +266,78 @@ class Plan:
     def close(self) -> None:
         if self.handle:
             vspec_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _BankDesc(ctypes.Structure):
+    _fields_ = [("nchan", ctypes.c_int), ("ntaps", ctypes.c_int), ("npol", ctypes.c_int),
+                ("mode", ctypes.c_int), ("window", ctypes.c_int)]
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[_addr(p) for p in ptrs])
+    return arr
+
+
+class Batch:
+    """Owns a vspec batch: one plan per bank, executed by one CUDA-graph launch."""
+
+    def __init__(self, banks):
+        """banks: sequence of (nchan, ntaps, npol, mode, window)."""
+        self.banks = [tuple(b) for b in banks]
+        descs = (_BankDesc * len(self.banks))(*[_BankDesc(*b) for b in self.banks])
+        h = ctypes.c_void_p()
+        self.handle = None
+        st = load().vspec_batch_create(ctypes.byref(h), len(self.banks), ctypes.addressof(descs))
+        if st != OK:
+            raise VspecError(st, "vspec_batch_create")
+        self.handle = h.value
+
+    def out_floats(self, i: int) -> int:
+        nchan, _, npol, _, _ = self.banks[i]
+        return nchan * (4 if npol == 2 else 1)
+
+    def _args(self, d_in, nspectra, d_accum):
+        ins = _ptr_array(d_in)
+        ns = (ctypes.c_int * len(nspectra))(*nspectra)
+        accs = _ptr_array(d_accum)
+        return ins, ns, accs
+
+    def execute(self, d_in, nspectra, d_accum, stream=None) -> None:
+        ins, ns, accs = self._args(d_in, nspectra, d_accum)
+        st = load().vspec_batch_execute(self.handle, ctypes.addressof(ins), ctypes.addressof(ns),
+                                        ctypes.addressof(accs), _stream(stream))
+        if st != OK:
+            raise VspecError(st, "vspec_batch_execute")
+
+    def autotune(self, d_in, nspectra, d_accum, stream=None, reps: int = 3) -> list:
+        ins, ns, accs = self._args(d_in, nspectra, d_accum)
+        st = load().vspec_batch_autotune(self.handle, ctypes.addressof(ins), ctypes.addressof(ns),
+                                         ctypes.addressof(accs), _stream(stream), reps)
+        if st != OK:
+            raise VspecError(st, "vspec_batch_autotune")
+        out = []
+        for i in range(len(self.banks)):
+            f = ctypes.c_uint()
+            load().vspec_batch_bank_flags(self.handle, i, ctypes.byref(f))
+            out.append(int(f.value))
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            load().vspec_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -179,3 +179,75 @@ def test_error_paths_on_device():
     with pytest.raises(vspec.VspecError) as e:
         vspec.Plan(1 << 20, 8, 2, PFB, WIN_HANN)
     assert e.value.status == vspec.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (1024, 8, 1, PFB, WIN_HANN, 70),
+                                 (131072, 1, 2, DIRECT, WIN_RECT, 40)])
+def test_execute_host_pipeline_matches_oracle(oracle_mod, cfg):
+    """Host input -> host output with overlapped chunked copies (the paper's
+    copy / compute / copy loop): several chunks, and a second call that must
+    overwrite, not add to, the output."""
+    from paper_1411_0436_gb300.vspec import Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0,
+                tones=(Tone(25.0, n * 0.21 + 0.3, (0,)),))
+    x = workloads.generate(bank, 77 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    with Plan(n, p, npol, mode, win) as plan:
+        h_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).pin_memory()
+        h_out = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            h_out.fill_(123.0)
+            plan.execute_host(h_in, s, h_out)
+            torch.cuda.synchronize()
+            got = h_out.numpy().astype(np.float64)
+            assert_close(got.reshape(o.shape), o, what=f"{cfg} host pipeline")
+
+
+def test_batch_graph_matches_single_banks(oracle_mod):
+    """Banks of different sizes and modes in one CUDA-graph launch give what
+    one plan per bank gives; replays and re-captures (new pointers) agree."""
+    from paper_1411_0436_gb300.vspec import Batch
+    banks = [Bank(1024, 8, 2, PFB, WIN_HANN, 40), Bank(4096, 1, 2, DIRECT, WIN_RECT, 20),
+             Bank(16384, 8, 2, PFB, WIN_HANN, 12), Bank(32768, 8, 2, PFB, WIN_HANN, 9),
+             Bank(65536, 1, 2, DIRECT, WIN_RECT, 4), Bank(2048, 8, 1, PFB, WIN_HAMMING, 30)]
+    xs = [workloads.generate(b, 500 + i) for i, b in enumerate(banks)]
+    refs = [run_oracle(oracle_mod, b, x) for b, x in zip(banks, xs)]
+    with Batch([(b.nchan, b.ntaps, b.npol, b.mode, b.window) for b in banks]) as batch:
+        d_in = [torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda() for x in xs]
+        accs = [torch.zeros(batch.out_floats(i), dtype=torch.float32, device="cuda") for i in range(len(banks))]
+        ns = [b.nspectra for b in banks]
+        flags = batch.autotune(d_in, ns, accs, reps=2)
+        assert len(flags) == len(banks)
+        for rep in range(3):   # capture, replay, replay
+            for a in accs:
+                a.zero_()
+            batch.execute(d_in, ns, accs)
+            torch.cuda.synchronize()
+            for b, a, o in zip(banks, accs, refs):
+                assert_close(a.cpu().numpy().astype(np.float64).reshape(o.shape), o, what=f"batch {b.nchan} rep {rep}")
+        accs2 = [torch.zeros_like(a) for a in accs]   # new pointers: re-capture
+        batch.execute(d_in, ns, accs2)
+        torch.cuda.synchronize()
+        for a, a2 in zip(accs, accs2):
+            assert torch.equal(a, a2)
+
+
+def test_plans_of_different_sizes_coexist():
+    """A plan keeps working after another plan of the same kernels but smaller
+    shared-memory needs was created (the kernels' shared-memory cap is shared)."""
+    big = Bank(262144, 8, 2, PFB, WIN_HANN, 2)
+    small = Bank(4096, 8, 2, PFB, WIN_HANN, 3)
+    from paper_1411_0436_gb300.vspec import PLAN_TWO_KERNEL, Plan
+    xb = workloads.generate(big, 1)
+    xs = workloads.generate(small, 2)
+    with Plan(big.nchan, 8, 2, PFB, WIN_HANN) as pb:
+        with Plan(small.nchan, 8, 2, PFB, WIN_HANN, PLAN_TWO_KERNEL) as ps:
+            db = torch.from_numpy(xb.view(np.uint8).reshape(-1)).cuda()
+            ds = torch.from_numpy(xs.view(np.uint8).reshape(-1)).cuda()
+            ab = torch.zeros(pb.out_floats, device="cuda")
+            as_ = torch.zeros(ps.out_floats, device="cuda")
+            ps.execute(ds, small.nspectra, as_)
+            pb.execute(db, big.nspectra, ab)
+            torch.cuda.synchronize()
+            assert torch.isfinite(ab).all() and ab.abs().sum() > 0
