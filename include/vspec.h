@@ -92,6 +92,22 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
 VSPEC_API vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int npol,
                                             vspec_mode mode, vspec_window window, unsigned flags);
 
+/*
+ * Plan for a sub-band mode: nsub sub-bands (1..16) of nchan channels each,
+ * every one channelized like a plan of vspec_plan_create_ex. VEGAS's
+ * eight-sub-band modes (§3, Table 1) run 16 FFTs in parallel: 8 sub-bands x
+ * 2 polarisations (§4, initialisation). Layouts of vspec_execute and the
+ * other calls on such a plan:
+ *   input   int8 [(nspectra + P_eff - 1) * nchan][nsub][npol][re, im]
+ *           (the sub-bands of one time sample are adjacent);
+ *   output  [nsub][nchan] of float4 (npol == 2) or float (npol == 1).
+ * Each call copies chunks of about 64 MiB of input into sub-band-contiguous
+ * order in plan-owned scratch, then channelizes every sub-band. nsub == 1 is
+ * exactly vspec_plan_create_ex.
+ */
+VSPEC_API vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int npol, int nsub,
+                                            vspec_mode mode, vspec_window window, unsigned flags);
+
 /* Release a plan and all device memory it owns. NULL is accepted. The caller
  * must make sure no work using the plan is still running on any stream. */
 VSPEC_API vspec_status vspec_plan_destroy(vspec_plan *plan);

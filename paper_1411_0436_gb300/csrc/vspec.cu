@@ -127,6 +127,10 @@ struct vspec_plan {
     size_t smemF = 0;
     const void *kernelF = nullptr;
     unsigned flags = 0;
+    // sub-bands: input [time][nsub][pol][re, im], output [nsub][nchan]
+    int nsub = 1;
+    int sb_chunk = 0;          // spectra per de-interleaved chunk
+    int8_t *sb_scratch = nullptr;
     // instrumentation (vspec_plan_set_profiling)
     struct Rec {
         int kind;
@@ -267,6 +271,7 @@ void free_plan(vspec_plan *p) {
     cudaFree(p->invB);
     cudaFree(p->Z);
     cudaFree(p->partial);
+    cudaFree(p->sb_scratch);
     delete p;
 }
 
@@ -568,6 +573,29 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
     return VSPEC_OK;
 }
 
+vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int npol, int nsub,
+                                  vspec_mode mode, vspec_window window, unsigned flags) {
+    if (!out) return VSPEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nsub < 1 || nsub > 16) return VSPEC_ERR_INVALID_ARG;
+    vspec_status st = vspec_plan_create_ex(out, nchan, ntaps, npol, mode, window, flags);
+    if (st != VSPEC_OK || nsub == 1) return st;
+    vspec_plan *p = *out;
+    p->nsub = nsub;
+    const int Peff = mode == VSPEC_PFB ? ntaps : 1;
+    const size_t per_spec = (size_t)nchan * npol * 2;  // bytes of one sub-band per spectrum
+    p->sb_chunk = (int)std::max<size_t>(1, (64u << 20) / (per_spec * nsub));
+    size_t tot = 0;
+    st = dev_alloc((void **)&p->sb_scratch, (size_t)nsub * (p->sb_chunk + Peff - 1) * per_spec, &tot);
+    if (st != VSPEC_OK) {
+        free_plan(p);
+        *out = nullptr;
+        return st;
+    }
+    p->scratch_bytes += tot;
+    return VSPEC_OK;
+}
+
 vspec_status vspec_plan_destroy(vspec_plan *plan) {
     free_plan(plan);
     return VSPEC_OK;
@@ -580,12 +608,48 @@ vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int 
     return VSPEC_OK;
 }
 
+static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
+                                cudaStream_t st);
+
 vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
                            void *stream) {
     if (!plan || !d_in || !d_accum || nspectra < 0) return VSPEC_ERR_INVALID_ARG;
     if (!aligned16(d_in) || !aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
     if (nspectra == 0) return VSPEC_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    vspec_plan *p = plan;
+    if (p->nsub == 1) return execute_one(p, d_in, nspectra, d_accum, st);
+    // sub-band modes: de-interleave a chunk of spectra, then every sub-band
+    const int Peff = p->mode == VSPEC_PFB ? p->P : 1;
+    const size_t wbytes = (size_t)p->npol * 2;             // one sample of every polarisation
+    const long long slot = (long long)(p->sb_chunk + Peff - 1) * p->N;  // samples per slot
+    const size_t outw = (size_t)p->N * (p->npol == 2 ? 4 : 1);
+    for (int s0 = 0; s0 < nspectra; s0 += p->sb_chunk) {
+        const int cnt = std::min(p->sb_chunk, nspectra - s0);
+        const long long M = (long long)(cnt + Peff - 1) * p->N;
+        const int8_t *src = d_in + (size_t)s0 * p->N * p->nsub * wbytes;
+        const int blocks = (int)((M + 255) / 256);
+        const size_t smem = (size_t)256 * (p->nsub + 1) * wbytes;
+        if (p->npol == 2)
+            vspec::deinterleave_kernel<uint32_t><<<blocks, 256, smem, st>>>(
+                reinterpret_cast<const uint32_t *>(src), reinterpret_cast<uint32_t *>(p->sb_scratch),
+                p->nsub, M, slot);
+        else
+            vspec::deinterleave_kernel<uint16_t><<<blocks, 256, smem, st>>>(
+                reinterpret_cast<const uint16_t *>(src), reinterpret_cast<uint16_t *>(p->sb_scratch),
+                p->nsub, M, slot);
+        VSPEC_CUDA(cudaGetLastError());
+        for (int b = 0; b < p->nsub; b++) {
+            vspec_status r = execute_one(p, p->sb_scratch + (size_t)b * slot * wbytes, cnt,
+                                         d_accum + (size_t)b * outw, st);
+            if (r != VSPEC_OK) return r;
+        }
+    }
+    return VSPEC_OK;
+}
+
+static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
+                                cudaStream_t st) {
     vspec_plan *p = plan;
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
 
@@ -730,7 +794,7 @@ vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset, cons
 // Spectra per chunk of the host-input pipeline: about 32 MiB of input per
 // staging buffer (at least 16 spectra), so copies and compute overlap.
 static int host_chunk_spectra(const vspec_plan *p) {
-    const size_t per = (size_t)p->N * p->npol * 2;
+    const size_t per = (size_t)p->N * p->nsub * p->npol * 2;
     return (int)std::max<size_t>(16, (32u << 20) / per);
 }
 
@@ -740,8 +804,8 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     vspec_plan *p = plan;
     cudaStream_t st = (cudaStream_t)stream;
     const int Peff = p->mode == VSPEC_PFB ? p->P : 1;
-    const size_t frame = (size_t)p->N * p->npol * 2;
-    const size_t out_bytes = (size_t)p->N * (p->npol == 2 ? 4 : 1) * sizeof(float);
+    const size_t frame = (size_t)p->N * p->nsub * p->npol * 2;
+    const size_t out_bytes = (size_t)p->nsub * p->N * (p->npol == 2 ? 4 : 1) * sizeof(float);
     if (!p->host_ready) {
         p->stage_spectra = host_chunk_spectra(p);
         const size_t sbytes = (size_t)(p->stage_spectra + Peff - 1) * frame;
@@ -791,7 +855,7 @@ vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *st
     if (!plan || !d_accum) return VSPEC_ERR_INVALID_ARG;
     if (!aligned16(d_accum)) return VSPEC_ERR_ALIGNMENT;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)plan->N * (plan->npol == 2 ? 4 : 1) * sizeof(float);
+    const size_t bytes = (size_t)plan->nsub * plan->N * (plan->npol == 2 ? 4 : 1) * sizeof(float);
     if (h_out) VSPEC_CUDA(cudaMemcpyAsync(h_out, d_accum, bytes, cudaMemcpyDeviceToHost, st));
     VSPEC_CUDA(cudaMemsetAsync(d_accum, 0, bytes, st));
     return VSPEC_OK;

@@ -352,6 +352,31 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
     }
 }
 
+// ------------------------------------------------------------ sub-bands --
+// Eight-sub-band modes (16 FFTs in parallel, §4): the input interleaves nsub
+// sub-bands per time sample, [time][sub][pol][re, im]. This kernel copies a
+// run of M time samples of every sub-band into sub-band-contiguous slots,
+// out[b * slot + m] = in[m * nsub + b], through a shared-memory tile so that
+// both sides are coalesced. W is one sample of every polarisation (4 bytes
+// dual-pol, 2 bytes single-pol).
+template <typename W>
+__global__ void deinterleave_kernel(const W *in, W *out, int nsub, long long M, long long slot) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W *tile = reinterpret_cast<W *>(smem_raw);  // [256][nsub + 1]
+    const long long m0 = (long long)blockIdx.x * 256;
+    const int cnt = (int)min(256LL, M - m0);
+    const int ld = nsub + 1;
+    for (int e = threadIdx.x; e < cnt * nsub; e += blockDim.x) {
+        const int m = e / nsub, b = e - m * nsub;
+        tile[m * ld + b] = in[(m0 + m) * nsub + b];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * nsub; e += blockDim.x) {
+        const int b = e / cnt, m = e - b * cnt;
+        out[(long long)b * slot + m0 + m] = tile[m * ld + b];
+    }
+}
+
 // ------------------------------------------------------------------ reduce --
 // d_accum[k] += sum over groups of partial[g][posA(k2) * N1 + posB(k1)].
 template <int NPOL>

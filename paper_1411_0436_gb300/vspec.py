@@ -66,6 +66,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_create.restype = i
         lib.vspec_plan_create_ex.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, ctypes.c_uint]
         lib.vspec_plan_create_ex.restype = i
+        lib.vspec_plan_create_sb.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, ctypes.c_uint]
+        lib.vspec_plan_create_sb.restype = i
         lib.vspec_plan_destroy.argtypes = [vp]
         lib.vspec_plan_destroy.restype = i
         lib.vspec_execute.argtypes = [vp, vp, i, vp, vp]
@@ -139,6 +141,15 @@ def vspec_plan_create_ex(nchan: int, ntaps: int, npol: int, mode: int, window: i
     st = load().vspec_plan_create_ex(ctypes.byref(h), nchan, ntaps, npol, mode, window, flags)
     if st != OK:
         raise VspecError(st, "vspec_plan_create_ex")
+    return h.value
+
+
+def vspec_plan_create_sb(nchan: int, ntaps: int, npol: int, nsub: int, mode: int, window: int,
+                         flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = load().vspec_plan_create_sb(ctypes.byref(h), nchan, ntaps, npol, nsub, mode, window, flags)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_create_sb")
     return h.value
 
 
@@ -223,18 +234,19 @@ class Plan:
     """Owns one vspec plan; checks tensor shapes before calling the library."""
 
     def __init__(self, nchan: int, ntaps: int = 8, npol: int = 2, mode: int = PFB,
-                 window: int = WIN_HANN, flags: int = 0):
+                 window: int = WIN_HANN, flags: int = 0, nsub: int = 1):
         self.nchan, self.ntaps, self.npol, self.mode, self.window = nchan, ntaps, npol, mode, window
+        self.nsub = nsub
         self.taps_used = 1 if mode == DIRECT else ntaps
         self.handle = None
-        self.handle = vspec_plan_create_ex(nchan, ntaps, npol, mode, window, flags)
+        self.handle = vspec_plan_create_sb(nchan, ntaps, npol, nsub, mode, window, flags)
 
     @property
     def out_floats(self) -> int:
-        return self.nchan * (4 if self.npol == 2 else 1)
+        return self.nsub * self.nchan * (4 if self.npol == 2 else 1)
 
     def input_bytes(self, nspectra: int) -> int:
-        return (nspectra + self.taps_used - 1) * self.nchan * self.npol * 2
+        return (nspectra + self.taps_used - 1) * self.nchan * self.nsub * self.npol * 2
 
     def execute(self, d_in, nspectra: int, d_accum, stream=None) -> None:
         if hasattr(d_in, "is_cuda"):

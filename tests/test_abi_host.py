@@ -47,6 +47,13 @@ def test_plan_create_ex_rejects_unknown_flags(lib):
     assert h.value is None
 
 
+@pytest.mark.parametrize("nsub", [0, 17, -1])
+def test_plan_create_sb_rejects_bad_subband_counts(lib, nsub):
+    h = ctypes.c_void_p(5)
+    assert lib.vspec_plan_create_sb(ctypes.byref(h), 4096, 8, 2, nsub, 0, 1, 0) == vspec.ERR_INVALID_ARG
+    assert h.value is None
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.vspec_plan_create(None, 1024, 8, 2, 0, 1) == vspec.ERR_INVALID_ARG
     assert lib.vspec_execute(None, 16, 1, 16, None) == vspec.ERR_INVALID_ARG
