@@ -272,6 +272,19 @@ VSPEC_API vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *co
                                             void *stream, int reps);
 VSPEC_API vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags);
 
+/*
+ * Batched 16-point DFTs on the tensor cores (tcgen05.mma, bf16 operands,
+ * fp32 accumulation in tensor memory): y[b][k] = sum_n x[b][n] exp(-2 pi i n k
+ * / 16) for b < batch, the radix-16 stage of §4's FFT as a dense contraction.
+ *   d_x, d_y  device complex float [batch][16] (re, im interleaved);
+ *   terms     1: bf16 operands (about 8 significant bits); 3: hi/lo split of
+ *             both operands, X_hi F_hi + X_hi F_lo + X_lo F_hi (about 16 bits).
+ * Synchronises `stream` before returning. Errors: VSPEC_ERR_INVALID_ARG,
+ * VSPEC_ERR_ALIGNMENT, VSPEC_ERR_CUDA, VSPEC_ERR_DEVICE_TIMEOUT (the bounded
+ * wait for the tensor cores gave up).
+ */
+VSPEC_API vspec_status vspec_tc_dft16(const float *d_x, float *d_y, int batch, int terms, void *stream);
+
 /* Static, human-readable text for a status code. */
 VSPEC_API const char *vspec_status_string(vspec_status status);
 

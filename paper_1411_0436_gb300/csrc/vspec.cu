@@ -19,6 +19,7 @@
 #include "vspec_fused.cuh"
 #include "vspec_fused_w.cuh"
 #include "vspec_kernels.cuh"
+#include "vspec_tc.cuh"
 
 using vspec::Pass;
 
@@ -849,6 +850,23 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     VSPEC_CUDA(cudaEventRecord(p->ev_done, p->comp_st));
     VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
     return VSPEC_OK;
+}
+
+vspec_status vspec_tc_dft16(const float *d_x, float *d_y, int batch, int terms, void *stream) {
+    if (!d_x || !d_y || batch < 0 || (terms != 1 && terms != 3)) return VSPEC_ERR_INVALID_ARG;
+    if (!aligned16(d_x) || !aligned16(d_y)) return VSPEC_ERR_ALIGNMENT;
+    if (batch == 0) return VSPEC_OK;
+    static int *d_status = nullptr;  // one int per process for the bounded-wait flag
+    if (!d_status) VSPEC_CUDA(cudaMalloc(&d_status, sizeof(int)));
+    cudaStream_t st = (cudaStream_t)stream;
+    VSPEC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+    vspec::tc::dft16_kernel<<<(batch + 127) / 128, 128, 0, st>>>(
+        reinterpret_cast<const float2 *>(d_x), reinterpret_cast<float2 *>(d_y), batch, terms, d_status);
+    VSPEC_CUDA(cudaGetLastError());
+    int h = 0;
+    VSPEC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VSPEC_CUDA(cudaStreamSynchronize(st));
+    return h ? VSPEC_ERR_DEVICE_TIMEOUT : VSPEC_OK;
 }
 
 vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *stream) {

@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_autotune.restype = i
         lib.vspec_batch_bank_flags.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint)]
         lib.vspec_batch_bank_flags.restype = i
+        lib.vspec_tc_dft16.argtypes = [vp, vp, i, i, vp]
+        lib.vspec_tc_dft16.restype = i
         lib.vspec_execute_host.argtypes = [vp, vp, i, vp, vp]
         lib.vspec_execute_host.restype = i
         lib.vspec_execute_noalloc.argtypes = [vp, i, i, i, i, i, i, vp, vp]
@@ -222,6 +224,12 @@ def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, wi
                                       _addr(d_accum), _stream(stream))
     if st != OK:
         raise VspecError(st, "vspec_execute_noalloc")
+
+
+def vspec_tc_dft16(d_x, d_y, batch: int, terms: int = 3, stream=None) -> None:
+    st = load().vspec_tc_dft16(_addr(d_x), _addr(d_y), batch, terms, _stream(stream))
+    if st != OK:
+        raise VspecError(st, "vspec_tc_dft16")
 
 
 def vspec_status_string(status: int) -> str:
