@@ -84,6 +84,11 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
 /* Plan flags for vspec_plan_create_ex. */
 #define VSPEC_PLAN_TWO_KERNEL 1u /* use the general two-kernel path even where the one-pass
                                     fused path applies (for comparison and testing) */
+#define VSPEC_PLAN_TENSOR 2u     /* two-kernel path with the first radix-16 pass of every
+                                    2048-point row on the tensor cores (bf16 hi/lo operands,
+                                    fp32 accumulation, see vspec_tc_dft16); dual-pol only,
+                                    nchan 2^11..2^19 where the rows are 2048 points; other
+                                    sizes return VSPEC_ERR_UNSUPPORTED */
 
 /*
  * vspec_plan_create with flags (a bitwise OR of VSPEC_PLAN_* values; 0 gives
@@ -107,6 +112,13 @@ VSPEC_API vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int nta
  */
 VSPEC_API vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int npol, int nsub,
                                             vspec_mode mode, vspec_window window, unsigned flags);
+
+/*
+ * Synchronise with the device and report whether a bounded device-side wait
+ * of this plan's kernels expired since the last check (VSPEC_ERR_DEVICE_TIMEOUT;
+ * the flag is then cleared). Plans without such waits return VSPEC_OK.
+ */
+VSPEC_API vspec_status vspec_plan_check(vspec_plan *plan);
 
 /* Release a plan and all device memory it owns. NULL is accepted. The caller
  * must make sure no work using the plan is still running on any stream. */

@@ -20,6 +20,7 @@
 #include "vspec_fused_w.cuh"
 #include "vspec_kernels.cuh"
 #include "vspec_tc.cuh"
+#include "vspec_kernels_tc.cuh"
 
 using vspec::Pass;
 
@@ -128,6 +129,8 @@ struct vspec_plan {
     size_t smemF = 0;
     const void *kernelF = nullptr;
     unsigned flags = 0;
+    bool tc = false;           // first row pass on the tensor cores
+    int *tc_status = nullptr;  // bounded-wait flag of the tensor-core kernel
     // sub-bands: input [time][nsub][pol][re, im], output [nsub][nchan]
     int nsub = 1;
     int sb_chunk = 0;          // spectra per de-interleaved chunk
@@ -273,6 +276,7 @@ void free_plan(vspec_plan *p) {
     cudaFree(p->Z);
     cudaFree(p->partial);
     cudaFree(p->sb_scratch);
+    cudaFree(p->tc_status);
     delete p;
 }
 
@@ -393,8 +397,8 @@ vspec_status build_plan(vspec_plan *p) {
     const int N = p->N;
     const int e = ilog2(N);
     const bool pfb = p->mode == VSPEC_PFB;
-    if (!(p->flags & VSPEC_PLAN_TWO_KERNEL) && p->npol == 2 && N >= 2048 && N <= 32768 &&
-        (!pfb || p->P == 8))
+    if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR)) && p->npol == 2 && N >= 2048 &&
+        N <= 32768 && (!pfb || p->P == 8))
         return build_fused_plan(p);
     const int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
     const int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
@@ -449,11 +453,21 @@ vspec_status build_plan(vspec_plan *p) {
     int maxb = 1;
     for (const Pass &ps : p->passB) maxb = std::max(maxb, p->RB * (N1 / ps.r));
     p->TB = std::min(256, std::max(32, maxb));
+    if (p->flags & VSPEC_PLAN_TENSOR) {
+        if (p->npol != 2 || N1 != vspec::kTcN1 || p->RB != 1 || p->passB[0].r != 16) {
+            g_last_error = "tensor-core stage needs dual-pol and 2048-point rows (nchan 2^11 .. 2^19)";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        p->tc = true;
+        p->kernelB = (const void *)vspec::rowfft_detect_tc_kernel<3>;
+        p->TB = 256;
+    }
 
     const size_t elem = p->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
     p->smemA = (size_t)PT * N2 * C * elem;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
+    if (p->tc) p->smemB = vspec::tc_rowfft_smem();
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -483,6 +497,10 @@ vspec_status build_plan(vspec_plan *p) {
     if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
     if ((st = dev_alloc(&p->Z, (size_t)p->sc_max * N * elem, &tot))) return st;
     if ((st = dev_alloc(&p->partial, (size_t)p->groups_b * N * accel, &tot))) return st;
+    if (p->tc) {
+        if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
+        VSPEC_CUDA(cudaMemset(p->tc_status, 0, sizeof(int)));
+    }
     p->scratch_bytes = tot;
 
     // digit-reversal maps (host) -> inverse maps for the final scatter
@@ -559,7 +577,7 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
     p->npol = npol;
     p->mode = mode;
     p->window = window;
-    if (flags & ~(unsigned)VSPEC_PLAN_TWO_KERNEL) {
+    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR)) {
         delete p;
         *out = nullptr;
         return VSPEC_ERR_INVALID_ARG;
@@ -743,7 +761,8 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
         vspec_status r = launch(p, 0, sc, p->kernelA, dim3(blocksA, ga), dim3(p->TA), argsA, p->smemA, st);
         if (r != VSPEC_OK) return r;
         cb.sc = sc;
-        void *argsB[] = {&cb};
+        vspec::TcStatus ts{p->tc_status};
+        void *argsB[] = {&cb, &ts};
         r = launch(p, 1, sc, p->kernelB, dim3(p->N2 / p->RB, p->groups_b), dim3(p->TB), argsB, p->smemB, st);
         if (r != VSPEC_OK) return r;
     }
@@ -850,6 +869,17 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     VSPEC_CUDA(cudaEventRecord(p->ev_done, p->comp_st));
     VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
     return VSPEC_OK;
+}
+
+vspec_status vspec_plan_check(vspec_plan *plan) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (!plan->tc_status) return VSPEC_OK;
+    int h = 0;
+    VSPEC_CUDA(cudaMemcpy(&h, plan->tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!h) return VSPEC_OK;
+    VSPEC_CUDA(cudaMemset(plan->tc_status, 0, sizeof(int)));
+    g_last_error = "a bounded wait for the tensor cores expired";
+    return VSPEC_ERR_DEVICE_TIMEOUT;
 }
 
 vspec_status vspec_tc_dft16(const float *d_x, float *d_y, int batch, int terms, void *stream) {

@@ -27,6 +27,7 @@ ERR_OOM = -5
 ERR_DEVICE_TIMEOUT = -6
 
 PLAN_TWO_KERNEL = 1  # force the general two-kernel path
+PLAN_TENSOR = 2      # first 2048-point row pass on the tensor cores
 
 _lib = None
 
@@ -91,6 +92,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_autotune.restype = i
         lib.vspec_batch_bank_flags.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint)]
         lib.vspec_batch_bank_flags.restype = i
+        lib.vspec_plan_check.argtypes = [vp]
+        lib.vspec_plan_check.restype = i
         lib.vspec_tc_dft16.argtypes = [vp, vp, i, i, vp]
         lib.vspec_tc_dft16.restype = i
         lib.vspec_execute_host.argtypes = [vp, vp, i, vp, vp]
@@ -276,6 +279,12 @@ class Plan:
 
     def info(self):
         return vspec_plan_info(self.handle)
+
+    def check(self) -> None:
+        """Raise if a bounded device-side wait of this plan expired."""
+        st = load().vspec_plan_check(self.handle)
+        if st != OK:
+            raise VspecError(st, "vspec_plan_check")
 
     def set_profiling(self, enable: bool = True) -> None:
         vspec_plan_set_profiling(self.handle, enable)

@@ -17,6 +17,11 @@ import numpy as np
 ATOL = 1e-5
 U32 = 2.0 ** -24
 RTOL_FP32 = 64 * U32
+# Tensor-core path (first DFT pass with bf16 hi/lo operands, about 16
+# significant bits): 1e-3 of the spectrum RMS, plus 64 units of 2^-17 of the
+# channel's own value.
+ATOL_TC = 1e-3
+RTOL_TC = 64 * 2.0 ** -17
 
 
 def metrics(gpu: np.ndarray, ref: np.ndarray, atol: float = ATOL, rtol: float = RTOL_FP32) -> dict:

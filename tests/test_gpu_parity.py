@@ -273,3 +273,31 @@ def test_subband_mode_matches_oracle(oracle_mod, cfg):
     for b in range(nsub):
         o = run_oracle(oracle_mod, bank, np.ascontiguousarray(x[:, b]))
         assert_close(got[b].reshape(o.shape), o, what=f"{cfg} sub-band {b}")
+
+
+@pytest.mark.parametrize("cfg", [(4096, 8, 2, PFB, WIN_HANN, 11), (32768, 8, 2, PFB, WIN_HANN, 30),
+                                 (131072, 8, 2, PFB, WIN_HANN, 3), (524288, 1, 2, DIRECT, WIN_RECT, 2),
+                                 (65536, 1, 2, DIRECT, WIN_RECT, 5)])
+def test_tensor_core_plan_matches_oracle(oracle_mod, cfg):
+    """First row pass on the tensor cores (bf16 hi/lo): within the tensor-core
+    tolerance of the oracle."""
+    from parity_util import ATOL_TC, RTOL_TC, metrics
+    from paper_1411_0436_gb300.vspec import PLAN_TENSOR, Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3, tones=(Tone(40.0, n * 0.2 + 0.37, (0, 1)),))
+    x = workloads.generate(bank, 321 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    g = run_gpu(bank, x, flags=PLAN_TENSOR)
+    m = assert_close(g, o, atol=ATOL_TC, rtol=RTOL_TC, what=f"{cfg} tensor")
+    print(f"\n{cfg}: normalised max error {m['pure']:.3e} (fp32 path: "
+          f"{metrics(run_gpu(bank, x), o)['pure']:.3e})")
+    with Plan(n, p, npol, mode, win, PLAN_TENSOR) as plan:
+        plan.check()
+
+
+def test_tensor_core_plan_rejects_other_sizes():
+    from paper_1411_0436_gb300 import vspec
+    for args in [(1024, 8, 2, PFB, WIN_HANN), (262144, 8, 2, PFB, WIN_HANN), (32768, 8, 1, PFB, WIN_HANN)]:
+        with pytest.raises(vspec.VspecError) as e:
+            vspec.Plan(*args, flags=vspec.PLAN_TENSOR)
+        assert e.value.status == vspec.ERR_UNSUPPORTED

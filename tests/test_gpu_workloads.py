@@ -35,3 +35,19 @@ def test_workload_matches_oracle(oracle_mod, name, idx):
     m = assert_close(g, o, what=f"{name}[{idx}]")
     print(f"\n{name}[{idx}] N={bank.nchan} S={bank.nspectra}: normalised max err {m['pure']:.3e}, "
           f"tolerance use {m['ratio']:.3f}, gpu {t1 - t0:.2f}s oracle {t2 - t1:.1f}s")
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_workload_tensor_core_path(oracle_mod, name):
+    """The tensor-core form on the benchmark and precision-stress workloads:
+    within the tensor-core tolerance; the error is printed beside the FP32
+    path's."""
+    from parity_util import ATOL_TC, RTOL_TC, metrics
+    from paper_1411_0436_gb300.vspec import PLAN_TENSOR
+    bank = workloads.CONFIGS[name][0]
+    x = workloads.generate(bank, workloads.config_seed(name))
+    o = run_oracle(oracle_mod, bank, x)
+    g = run_gpu(bank, x, flags=PLAN_TENSOR)
+    m = assert_close(g, o, atol=ATOL_TC, rtol=RTOL_TC, what=f"{name} tensor")
+    f = metrics(run_gpu(bank, x), o)
+    print(f"\n{name}: tensor-core path normalised max error {m['pure']:.3e}, fp32 path {f['pure']:.3e}")
