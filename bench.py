@@ -300,12 +300,58 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(plan.out_floats * 4),
                "steps": e2e_steps, "api": "vspec_execute_host"}
 
+    # TC-FP16 vs FP32: the same dump through the tensor-core plan and through
+    # the FP32 two-kernel plan (rank 0 only), with their errors against the
+    # oracle when the CPU baseline runs
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        from paper_1411_0436_gb300.vspec import PLAN_TENSOR, PLAN_TWO_KERNEL
+        variants = {}
+        vsteps = max(3, min(args.steps, 50))
+        for key, flags in (("tensor_core_bf16_hilo", PLAN_TENSOR), ("fp32_two_kernel", PLAN_TWO_KERNEL)):
+            vp = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window, flags)
+            vacc = torch.zeros(vp.out_floats, dtype=torch.float32, device=dev)
+            for _ in range(3):
+                vp.execute(d_in, S, vacc, stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(vsteps)]
+            for a, b in ev:
+                flush.fill_(3)
+                a.record(stream)
+                vp.execute(d_in, S, vacc, stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            vms = sum(a.elapsed_time(b) for a, b in ev) / vsteps
+            vacc.zero_()
+            vp.execute(d_in, S, vacc, stream)
+            torch.cuda.synchronize()
+            variants[key] = {"value": S * n / (vms * 1e-3) / 1e9, "unit": "GHz", "ms_per_step": vms,
+                             "out": vacc.cpu().numpy().astype(np.float64).reshape(n, 4)}
+            vp.close()
+        acc.zero_()
+        plan.execute(d_in, S, acc, stream)
+        torch.cuda.synchronize()
+        variants["fp32_fused"] = {"value": value, "unit": "GHz", "ms_per_step": total_ms / args.steps,
+                                  "out": acc.cpu().numpy().astype(np.float64).reshape(n, 4)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         ghz, s_used, runs, dt = _oracle_rate(bank, x, 12.0, threads)
         cpu = {"value": ghz, "unit": "GHz", "cores": threads, "kind": "oracle",
                "sample": f"first {s_used} of {S} spectra of the same input, {runs} runs, {dt:.1f} s"}
+        if variants:
+            import oracle
+            ref = oracle.channelize(x, n, bank.ntaps, bank.npol, S, bank.mode, bank.window, nthreads=threads)
+            rms = np.sqrt(np.mean(ref ** 2, axis=0))
+            scale = np.array([rms[0], rms[1], np.sqrt(rms[0] * rms[1]), np.sqrt(rms[0] * rms[1])])
+            for v in variants.values():
+                v["max_err_norm_rms"] = float(np.max(np.abs(v["out"] - ref) / scale))
+    if variants:
+        for v in variants.values():
+            v.pop("out", None)
+        variants["tc_speedup_over_fp32_fused"] = (variants["tensor_core_bf16_hilo"]["value"] /
+                                                  variants["fp32_fused"]["value"])
 
     plan.close()
     if rank == 0:
@@ -328,6 +374,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "tc_vs_fp32": variants,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} | {"samples": clk["samples"]},
             "complex_gsps": 2 * value,
         }
@@ -391,6 +438,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the tensor-core and two-kernel comparison runs")
     ap.add_argument("--config", choices=["c2", "c5"], default="c2",
                     help="c2: the 32768-channel PFB dump (default); c5: the batched multi-beam workload")
     args = ap.parse_args()

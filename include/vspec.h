@@ -89,6 +89,11 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
                                     fp32 accumulation, see vspec_tc_dft16); dual-pol only,
                                     nchan 2^11..2^19 where the rows are 2048 points; other
                                     sizes return VSPEC_ERR_UNSUPPORTED */
+#define VSPEC_PLAN_KAHAN 4u      /* compensated (Kahan) FP32 accumulation at every level: over
+                                    spectra in the kernel, across groups and into the caller's
+                                    accumulator through a plan-owned compensation buffer that
+                                    vspec_dump clears; uses the two-kernel path (combinable with
+                                    VSPEC_PLAN_TENSOR). With it, keep one accumulator per plan. */
 
 /*
  * vspec_plan_create with flags (a bitwise OR of VSPEC_PLAN_* values; 0 gives

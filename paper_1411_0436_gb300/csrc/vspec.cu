@@ -130,6 +130,8 @@ struct vspec_plan {
     const void *kernelF = nullptr;
     unsigned flags = 0;
     bool tc = false;           // first row pass on the tensor cores
+    bool kahan = false;        // compensated accumulation at every level
+    void *partial_comp = nullptr, *out_comp = nullptr;
     int *tc_status = nullptr;  // bounded-wait flag of the tensor-core kernel
     // sub-bands: input [time][nsub][pol][re, im], output [nsub][nchan]
     int nsub = 1;
@@ -277,6 +279,8 @@ void free_plan(vspec_plan *p) {
     cudaFree(p->partial);
     cudaFree(p->sb_scratch);
     cudaFree(p->tc_status);
+    cudaFree(p->partial_comp);
+    cudaFree(p->out_comp);
     delete p;
 }
 
@@ -397,7 +401,7 @@ vspec_status build_plan(vspec_plan *p) {
     const int N = p->N;
     const int e = ilog2(N);
     const bool pfb = p->mode == VSPEC_PFB;
-    if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR)) && p->npol == 2 && N >= 2048 &&
+    if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN)) && p->npol == 2 && N >= 2048 &&
         N <= 32768 && (!pfb || p->P == 8))
         return build_fused_plan(p);
     const int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
@@ -459,15 +463,25 @@ vspec_status build_plan(vspec_plan *p) {
             return VSPEC_ERR_UNSUPPORTED;
         }
         p->tc = true;
-        p->kernelB = (const void *)vspec::rowfft_detect_tc_kernel<3>;
+        p->kernelB = (p->flags & VSPEC_PLAN_KAHAN) ? (const void *)vspec::rowfft_detect_tc_kernel<3, true>
+                                                   : (const void *)vspec::rowfft_detect_tc_kernel<3, false>;
         p->TB = 256;
+    }
+    if (p->flags & VSPEC_PLAN_KAHAN) {
+        p->kahan = true;
+        if (!p->tc)
+            p->kernelB = p->npol == 2 ? (const void *)vspec::rowfft_detect_kernel<2, true>
+                                      : (const void *)vspec::rowfft_detect_kernel<1, true>;
+        p->kernelR = p->npol == 2 ? (const void *)vspec::reduce_kahan_kernel<2>
+                                  : (const void *)vspec::reduce_kahan_kernel<1>;
     }
 
     const size_t elem = p->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
     p->smemA = (size_t)PT * N2 * C * elem;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
-    if (p->tc) p->smemB = vspec::tc_rowfft_smem();
+    if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
+    if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -500,6 +514,11 @@ vspec_status build_plan(vspec_plan *p) {
     if (p->tc) {
         if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
         VSPEC_CUDA(cudaMemset(p->tc_status, 0, sizeof(int)));
+    }
+    if (p->kahan) {
+        if ((st = dev_alloc(&p->partial_comp, (size_t)p->groups_b * N * accel, &tot))) return st;
+        if ((st = dev_alloc(&p->out_comp, (size_t)N * accel, &tot))) return st;
+        VSPEC_CUDA(cudaMemset(p->out_comp, 0, (size_t)N * accel));
     }
     p->scratch_bytes = tot;
 
@@ -577,7 +596,7 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
     p->npol = npol;
     p->mode = mode;
     p->window = window;
-    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR)) {
+    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN)) {
         delete p;
         *out = nullptr;
         return VSPEC_ERR_INVALID_ARG;
@@ -597,6 +616,10 @@ vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int np
     if (!out) return VSPEC_ERR_INVALID_ARG;
     *out = nullptr;
     if (nsub < 1 || nsub > 16) return VSPEC_ERR_INVALID_ARG;
+    if (nsub > 1 && (flags & VSPEC_PLAN_KAHAN)) {
+        g_last_error = "compensated accumulation is not available in sub-band modes";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
     vspec_status st = vspec_plan_create_ex(out, nchan, ntaps, npol, mode, window, flags);
     if (st != VSPEC_OK || nsub == 1) return st;
     vspec_plan *p = *out;
@@ -719,6 +742,7 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     }
 
     VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->groups_b * p->N * accel, st));
+    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)p->groups_b * p->N * accel, st));
 
     const int sc_full = std::min(nspectra, p->sc_max);
     const int blocksA = p->N1 / p->C;
@@ -741,6 +765,7 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     vspec::RowParams cb;
     cb.Z = p->Z;
     cb.partial = p->partial;
+    cb.partial_comp = p->partial_comp;
     cb.twB = p->twB;
     cb.N = p->N;
     cb.N1 = p->N1;
@@ -765,6 +790,16 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
         void *argsB[] = {&cb, &ts};
         r = launch(p, 1, sc, p->kernelB, dim3(p->N2 / p->RB, p->groups_b), dim3(p->TB), argsB, p->smemB, st);
         if (r != VSPEC_OK) return r;
+    }
+    if (p->kahan) {
+        const void *part = p->partial, *pcomp = p->partial_comp;
+        int groups = p->groups_b, N = p->N, N1 = p->N1, N2 = p->N2;
+        const int *ia = p->invA, *ib = p->invB;
+        void *outp = d_accum, *ocomp = p->out_comp;
+        void *argsR[] = {&part, &pcomp, &groups, &N, &N1, &N2, &ia, &ib, &outp, &ocomp};
+        vspec_status r = launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+        if (r != VSPEC_OK) return r;
+        return VSPEC_OK;
     }
     {
         const void *part = p->partial;
@@ -906,6 +941,7 @@ vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *st
     const size_t bytes = (size_t)plan->nsub * plan->N * (plan->npol == 2 ? 4 : 1) * sizeof(float);
     if (h_out) VSPEC_CUDA(cudaMemcpyAsync(h_out, d_accum, bytes, cudaMemcpyDeviceToHost, st));
     VSPEC_CUDA(cudaMemsetAsync(d_accum, 0, bytes, st));
+    if (plan->out_comp) VSPEC_CUDA(cudaMemsetAsync(plan->out_comp, 0, bytes / plan->nsub, st));
     return VSPEC_OK;
 }
 

@@ -55,6 +55,7 @@ struct ColParams {
 struct RowParams {
     const void *Z;       // chunk scratch written by kernel A
     void *partial;       // [group][pos][posB] of Elem::Acc, accumulated into
+    void *partial_comp;  // Kahan compensation of `partial` (compensated plans only)
     const float2 *twB;   // per-pass twiddles of the length-N1 row DFTs
     int N, N1, N2, RB, npass;
     Pass pass[kMaxPasses];
@@ -253,12 +254,46 @@ template <int NPOL> __device__ __forceinline__ void acc_add(float4 &a, float4 v)
 }
 __device__ __forceinline__ void acc_add1(float &a, float2 v) { a += fmaf(v.x, v.x, v.y * v.y); }
 
-template <int R, int NPOL>
+// Compensated (Kahan) summation a += v with running compensation c.
+__device__ __forceinline__ void kahan_add(float &a, float &c, float v) {
+    const float y = v - c;
+    const float t = a + y;
+    c = (t - a) - y;
+    a = t;
+}
+__device__ __forceinline__ void kahan_add(float4 &a, float4 &c, float4 v) {
+    kahan_add(a.x, c.x, v.x);
+    kahan_add(a.y, c.y, v.y);
+    kahan_add(a.z, c.z, v.z);
+    kahan_add(a.w, c.w, v.w);
+}
+// Fold the compensation into the value (Fast2Sum, exact since |c| <= |a|):
+// afterwards a is the correctly rounded a - c and a - c is unchanged.
+__device__ __forceinline__ void kahan_settle(float &a, float &c) {
+    const float t = a - c;
+    c = (t - a) + c;
+    a = t;
+}
+__device__ __forceinline__ void kahan_settle(float4 &a, float4 &c) {
+    kahan_settle(a.x, c.x);
+    kahan_settle(a.y, c.y);
+    kahan_settle(a.z, c.z);
+    kahan_settle(a.w, c.w);
+}
+__device__ __forceinline__ float4 detect4(float4 v) {
+    return make_float4(fmaf(v.x, v.x, v.y * v.y), fmaf(v.z, v.z, v.w * v.w), fmaf(v.x, v.z, v.y * v.w),
+                       fmaf(v.y, v.z, -v.x * v.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+template <int R, int NPOL, bool KAHAN = false>
 __device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::Acc *acc,
                                               const typename Elem<NPOL>::T *Zs, const Pass ps,
                                               bool first, bool last, int r, int b, int j,
-                                              int rowstride) {
+                                              int rowstride, typename Elem<NPOL>::Acc *comp = nullptr) {
     using T = typename Elem<NPOL>::T;
     const int base = b * ps.lb + j;
     T *row = data + r * rowstride;
@@ -286,13 +321,18 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<
         const int w = r * (p.N1 / R) + b;
 #pragma unroll
         for (int q = 0; q < R; q++) {
-            if constexpr (NPOL == 2) acc_add<2>(acc[q * U + w], v[q]);
-            else acc_add1(acc[q * U + w], v[q]);
+            if constexpr (KAHAN) {
+                if constexpr (NPOL == 2) kahan_add(acc[q * U + w], comp[q * U + w], detect4(v[q]));
+                else kahan_add(acc[q * U + w], comp[q * U + w], fmaf(v[q].x, v[q].x, v[q].y * v[q].y));
+            } else {
+                if constexpr (NPOL == 2) acc_add<2>(acc[q * U + w], v[q]);
+                else acc_add1(acc[q * U + w], v[q]);
+            }
         }
     }
 }
 
-template <int NPOL>
+template <int NPOL, bool KAHAN = false>
 __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_constant__ RowParams p) {
     using T = typename Elem<NPOL>::T;
     using A = typename Elem<NPOL>::Acc;
@@ -300,6 +340,7 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
     const int rowstride = p.N1 + (p.N1 >> 4);
     T *data = reinterpret_cast<T *>(smem_raw);
     A *acc = reinterpret_cast<A *>(data + p.RB * rowstride);
+    A *comp = acc + p.RB * p.N1;  // compensation (compensated plans only)
 
     const int g = blockIdx.y;
     const int s_beg = (int)((long long)p.sc * g / p.groups);
@@ -310,6 +351,7 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
     for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
         if constexpr (NPOL == 2) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         else acc[e] = 0.f;
+        if constexpr (KAHAN) comp[e] = acc[e];
     }
     __syncthreads();
 
@@ -324,10 +366,10 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
                 const int r = u / per_row, w = u - r * per_row;
                 const int b = w / ps.m, j = w - b * ps.m;
                 switch (ps.r) {
-                    case 2: row_butterfly<2, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
-                    case 4: row_butterfly<4, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
-                    case 8: row_butterfly<8, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
-                    default: row_butterfly<16, NPOL>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride); break;
+                    case 2: row_butterfly<2, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                    case 4: row_butterfly<4, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                    case 8: row_butterfly<8, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                    default: row_butterfly<16, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
                 }
             }
             __syncthreads();
@@ -342,7 +384,14 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
         const int q = e / U, w = e - q * U;
         const int r = w / (p.N1 / RL), b = w - r * (p.N1 / RL);
         const size_t o = (size_t)(blockIdx.x * p.RB + r) * p.N1 + b * RL + q;
-        if constexpr (NPOL == 2) {
+        if constexpr (KAHAN) {
+            A *pc = reinterpret_cast<A *>(p.partial_comp) + (size_t)g * p.N;
+            A a = part[o], c = pc[o];
+            if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[e], comp[e]));
+            else kahan_add(a, c, acc[e] - comp[e]);
+            part[o] = a;
+            pc[o] = c;
+        } else if constexpr (NPOL == 2) {
             float4 a = part[o];
             const float4 d = acc[e];
             part[o] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
@@ -401,6 +450,44 @@ __global__ void reduce_kernel(const void *partial, int groups, int N, int N1, in
         float s = pp[idx];
         for (int g = 1; g < groups; g++) s += pp[(size_t)g * N + idx];
         o[k] += s;
+    }
+}
+
+// Compensated reduce: Kahan sum of the compensated group partials, then a
+// compensated add into the caller's accumulator with the plan-owned
+// compensation out_comp (cleared by vspec_dump).
+template <int NPOL>
+__global__ void reduce_kahan_kernel(const void *partial, const void *partial_comp, int groups, int N, int N1,
+                                    int N2, const int *invA, const int *invB, void *out, void *out_comp) {
+    using A = typename Elem<NPOL>::Acc;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int k2 = k & (N2 - 1), k1 = k / N2;
+    const size_t idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
+    const A *pp = reinterpret_cast<const A *>(partial);
+    const A *pc = reinterpret_cast<const A *>(partial_comp);
+    A *o = reinterpret_cast<A *>(out);
+    A *oc = reinterpret_cast<A *>(out_comp);
+    A s, c;
+    if constexpr (NPOL == 2) {
+        s = make_float4(0.f, 0.f, 0.f, 0.f);
+        c = s;
+        for (int g = 0; g < groups; g++)
+            kahan_add(s, c, sub4(pp[(size_t)g * N + idx], pc[(size_t)g * N + idx]));
+        float4 a = o[k], ac = oc[k];
+        kahan_add(a, ac, sub4(s, c));
+        kahan_settle(a, ac);
+        o[k] = a;
+        oc[k] = ac;
+    } else {
+        s = 0.f;
+        c = 0.f;
+        for (int g = 0; g < groups; g++) kahan_add(s, c, pp[(size_t)g * N + idx] - pc[(size_t)g * N + idx]);
+        float a = o[k], ac = oc[k];
+        kahan_add(a, ac, s - c);
+        kahan_settle(a, ac);
+        o[k] = a;
+        oc[k] = ac;
     }
 }
 

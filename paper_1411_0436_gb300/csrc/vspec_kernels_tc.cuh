@@ -21,11 +21,11 @@ struct TcStatus {
 constexpr int kTcN1 = 2048;
 constexpr int kTcSmemOps = 4 * tc::kAPart + 2 * tc::kBPart;  // A0/A1 hi, lo and F hi, lo
 
-__host__ __device__ constexpr size_t tc_rowfft_smem() {
-    return (size_t)kTcSmemOps + (size_t)(kTcN1 + kTcN1 / 16) * 16 + (size_t)kTcN1 * 16;
+__host__ __device__ constexpr size_t tc_rowfft_smem(bool kahan) {
+    return (size_t)kTcSmemOps + (size_t)(kTcN1 + kTcN1 / 16) * 16 + (size_t)kTcN1 * 16 * (kahan ? 2 : 1);
 }
 
-template <int TERMS>
+template <int TERMS, bool KAHAN = false>
 __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_constant__ RowParams p,
                                                                   TcStatus ts) {
     using namespace tc;
@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     float4 *data = reinterpret_cast<float4 *>(smem_tc + kTcSmemOps);   // one row, padded
     const int rowstride = kTcN1 + kTcN1 / 16;
     float4 *acc = data + rowstride;
+    float4 *comp = acc + kTcN1;  // compensation (compensated plans only)
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ float2 w16[16];
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fill_w16(w16);
-    for (int e = tid; e < kTcN1; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = tid; e < kTcN1; e += blockDim.x) {
+        acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (KAHAN) comp[e] = acc[e];
+    }
     __syncthreads();
     stage_dft16_operand(bhi, blo, w16);
     fence_proxy_async();
@@ -116,10 +120,10 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
             for (int u = tid; u < per_row; u += blockDim.x) {
                 const int b = u / ps.m, jj = u - b * ps.m;
                 switch (ps.r) {
-                    case 2: row_butterfly<2, 2>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride); break;
-                    case 4: row_butterfly<4, 2>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride); break;
-                    case 8: row_butterfly<8, 2>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride); break;
-                    default: row_butterfly<16, 2>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride); break;
+                    case 2: row_butterfly<2, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                    case 4: row_butterfly<4, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                    case 8: row_butterfly<8, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                    default: row_butterfly<16, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
                 }
             }
             __syncthreads();
@@ -134,8 +138,16 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     for (int e = tid; e < kTcN1; e += blockDim.x) {
         const int q = e / U, b = e - q * U;
         float4 a = part[b * RL + q];
-        const float4 d = acc[e];
-        part[b * RL + q] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+        if constexpr (KAHAN) {
+            float4 *pc = reinterpret_cast<float4 *>(p.partial_comp) + (size_t)g * p.N + (size_t)blockIdx.x * kTcN1;
+            float4 c = pc[b * RL + q];
+            kahan_add(a, c, sub4(acc[e], comp[e]));
+            pc[b * RL + q] = c;
+            part[b * RL + q] = a;
+        } else {
+            const float4 d = acc[e];
+            part[b * RL + q] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

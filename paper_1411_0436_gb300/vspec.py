@@ -28,6 +28,7 @@ ERR_DEVICE_TIMEOUT = -6
 
 PLAN_TWO_KERNEL = 1  # force the general two-kernel path
 PLAN_TENSOR = 2      # first 2048-point row pass on the tensor cores
+PLAN_KAHAN = 4       # compensated accumulation
 
 _lib = None
 

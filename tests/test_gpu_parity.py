@@ -301,3 +301,31 @@ def test_tensor_core_plan_rejects_other_sizes():
         with pytest.raises(vspec.VspecError) as e:
             vspec.Plan(*args, flags=vspec.PLAN_TENSOR)
         assert e.value.status == vspec.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 67), (4096, 1, 1, DIRECT, WIN_RECT, 40),
+                                 (131072, 8, 2, PFB, WIN_HANN, 5)])
+def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
+    """Kahan accumulation (alone and with the tensor-core pass) stays within
+    the tolerances; dump clears the compensation with the accumulator."""
+    from parity_util import ATOL_TC, RTOL_TC, metrics
+    from paper_1411_0436_gb300.vspec import PLAN_KAHAN, PLAN_TENSOR, Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0,
+                tones=(Tone(50.0, n * 0.1 + 0.25, (0,)),))
+    x = workloads.generate(bank, 4000 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    mk = assert_close(run_gpu(bank, x, flags=PLAN_KAHAN), o, what=f"{cfg} kahan")
+    mp = metrics(run_gpu(bank, x, flags=1), o)
+    print(f"\n{cfg}: normalised max error plain {mp['pure']:.3e}, compensated {mk['pure']:.3e}")
+    if npol == 2:
+        assert_close(run_gpu(bank, x, flags=PLAN_KAHAN | PLAN_TENSOR), o, atol=ATOL_TC, rtol=RTOL_TC,
+                     what=f"{cfg} kahan+tensor")
+    with Plan(n, p, npol, mode, win, PLAN_KAHAN) as plan:  # twice, dump in between
+        d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        plan.execute(d_in, s, acc)
+        plan.dump(acc)
+        plan.execute(d_in, s, acc)
+        torch.cuda.synchronize()
+        assert_close(acc.cpu().numpy().astype(np.float64).reshape(o.shape), o, what=f"{cfg} after dump")

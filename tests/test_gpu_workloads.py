@@ -50,4 +50,9 @@ def test_workload_tensor_core_path(oracle_mod, name):
     g = run_gpu(bank, x, flags=PLAN_TENSOR)
     m = assert_close(g, o, atol=ATOL_TC, rtol=RTOL_TC, what=f"{name} tensor")
     f = metrics(run_gpu(bank, x), o)
-    print(f"\n{name}: tensor-core path normalised max error {m['pure']:.3e}, fp32 path {f['pure']:.3e}")
+    from paper_1411_0436_gb300.vspec import PLAN_KAHAN
+    k = assert_close(run_gpu(bank, x, flags=PLAN_KAHAN), o, what=f"{name} kahan")
+    tk = assert_close(run_gpu(bank, x, flags=PLAN_KAHAN | PLAN_TENSOR), o, atol=ATOL_TC, rtol=RTOL_TC,
+                      what=f"{name} tensor+kahan")
+    print(f"\n{name}: normalised max error: fp32 {f['pure']:.3e}, fp32+kahan {k['pure']:.3e}, "
+          f"tensor {m['pure']:.3e}, tensor+kahan {tk['pure']:.3e}")
