@@ -33,8 +33,15 @@ from paper_1411_0436_gb300 import workloads  # noqa: E402
 
 METRIC = "Dual-pol real-time bandwidth (GHz) & % HBM roofline, TC-FP16 vs FP32 FFT"
 CONFIG_NAME = "c2"
-WORKLOAD = ("dual-pol PFB, 32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra per dump, "
-            "int8 Gaussian sigma=20 with X/Y correlation 0.3 and two tones")
+WORKLOADS = {
+    "c1": "single-pol PFB, 1024 channels, 8 taps, Hann-windowed sinc, 64 spectra, tone at bin 123.4",
+    "c2": ("dual-pol PFB, 32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra per dump, "
+           "int8 Gaussian sigma=20 with X/Y correlation 0.3 and two tones"),
+    "c3": "dual-pol direct FFT, 524288 channels, 256 spectra per dump, int8 Gaussian sigma=20",
+    "c4": ("dual-pol PFB, 131072 channels, 8 taps, Hann-windowed sinc, 4096 spectra per dump, "
+           "sigma=4 with a tone 40 dB above the per-channel noise floor"),
+}
+WORKLOAD = WORKLOADS["c2"]
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
@@ -73,9 +80,9 @@ def _traffic(kernel: str, spectra_per_launch: float):
     return float(ent["dram_bytes_per_spectrum"]) * spectra_per_launch
 
 
-def beam_seed(rank: int) -> int:
+def beam_seed(rank: int, config: str = CONFIG_NAME) -> int:
     """Seed of rank `rank`'s beam: every rank channelizes independent input."""
-    return workloads.config_seed(CONFIG_NAME) + 7919 * rank
+    return workloads.config_seed(config) + 7919 * rank
 
 
 def reduce_max(value: float, dist=None, device=None) -> float:
@@ -209,9 +216,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    bank = workloads.CONFIGS[CONFIG_NAME][0]
+    config = args.config
+    bank = workloads.CONFIGS[config][0]
     # each rank is an independent beam: its own seeded input
-    x = workloads.generate(bank, beam_seed(rank))
+    x = workloads.generate(bank, beam_seed(rank, config))
     in_bytes = x.nbytes
     n, S = bank.nchan, bank.nspectra
     plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window)
@@ -304,7 +312,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # the FP32 two-kernel plan (rank 0 only), with their errors against the
     # oracle when the CPU baseline runs
     variants = None
-    if rank == 0 and world == 1 and not args.no_variants:
+    if rank == 0 and world == 1 and not args.no_variants and bank.npol == 2 and config in ("c2", "c4"):
         from paper_1411_0436_gb300.vspec import PLAN_TENSOR, PLAN_TWO_KERNEL
         variants = {}
         vsteps = max(3, min(args.steps, 50))
@@ -326,7 +334,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             vp.execute(d_in, S, vacc, stream)
             torch.cuda.synchronize()
             variants[key] = {"value": S * n / (vms * 1e-3) / 1e9, "unit": "GHz", "ms_per_step": vms,
-                             "out": vacc.cpu().numpy().astype(np.float64).reshape(n, 4)}
+                             "out": vacc.cpu().numpy().astype(np.float64).reshape(n, 4),
+                             "flags": flags}
             vp.close()
         acc.zero_()
         plan.execute(d_in, S, acc, stream)
@@ -343,6 +352,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if variants:
             import oracle
             ref = oracle.channelize(x, n, bank.ntaps, bank.npol, S, bank.mode, bank.window, nthreads=threads)
+            ref = ref.reshape(n, -1)
             rms = np.sqrt(np.mean(ref ** 2, axis=0))
             scale = np.array([rms[0], rms[1], np.sqrt(rms[0] * rms[1]), np.sqrt(rms[0] * rms[1])])
             for v in variants.values():
@@ -360,8 +370,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nchan": n, "ntaps": bank.ntaps, "npol": bank.npol,
-                       "nspectra": S, "input_bytes": int(in_bytes),
+            "config": {"workload": WORKLOADS[config], "name": config, "nchan": n, "ntaps": bank.ntaps,
+                       "npol": bank.npol, "nspectra": S, "input_bytes": int(in_bytes),
                        "l2": "flushed between steps (256 MiB write outside the timed interval)",
                        "parallelism": f"replicas x{world} (independent beams)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -430,6 +440,66 @@ def run_batch(args):
     }), flush=True)
 
 
+def run_sweep(args):
+    """Real-time bandwidth against FFT length and accumulation length (the
+    shape of the paper's Fig. 3, §5): 8-tap PFB and direct FFT, N = 2^10 ..
+    2^20, a = 1, 10, 100, 1000 spectra per call, device-resident input, and
+    the host-copy loop of §4 through vspec_execute_host where the input fits a
+    1 GiB pinned buffer. Inputs are random int8 drawn on the device (timing
+    only). One JSON line per case."""
+    import torch
+    from paper_1411_0436_gb300.vspec import Plan, VspecError
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    pinned = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    for mode, taps in ((workloads.PFB, 8), (workloads.DIRECT, 1)):
+        for e in range(10, 21):
+            n = 1 << e
+            try:
+                plan = Plan(n, taps, 2, mode, workloads.WIN_HANN if mode == workloads.PFB else workloads.WIN_RECT)
+            except VspecError as err:
+                print(json.dumps({"sweep": True, "mode": "pfb" if mode == workloads.PFB else "direct",
+                                  "nchan": n, "unsupported": str(err)}), flush=True)
+                continue
+            for a in (1, 10, 100, 1000):
+                nbytes = (a + taps - 1) * n * 4
+                if nbytes > (6 << 30):
+                    continue
+                d_in = torch.randint(-127, 128, (nbytes,), dtype=torch.int8, device=dev)
+                acc = torch.zeros(plan.out_floats, dtype=torch.float32, device=dev)
+                reps = max(3, min(20, int(2e8 // (a * n))))
+                for _ in range(2):
+                    plan.execute(d_in, a, acc, stream)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+                for t0, t1 in ev:
+                    flush.fill_(5)
+                    t0.record(stream)
+                    plan.execute(d_in, a, acc, stream)
+                    t1.record(stream)
+                torch.cuda.synchronize()
+                ms = sum(t0.elapsed_time(t1) for t0, t1 in ev) / reps
+                line = {"sweep": True, "mode": "pfb" if mode == workloads.PFB else "direct", "nchan": n,
+                        "spectra_per_call": a, "ghz_device": a * n / (ms * 1e-3) / 1e9, "ms_device": ms}
+                if nbytes <= pinned.numel():
+                    pinned[:nbytes].copy_(d_in.view(torch.uint8).cpu())
+                    h_out = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
+                    plan.execute_host(pinned, a, h_out, stream)
+                    torch.cuda.synchronize()
+                    t0 = torch.cuda.Event(enable_timing=True)
+                    t1 = torch.cuda.Event(enable_timing=True)
+                    t0.record(stream)
+                    for _ in range(reps):
+                        plan.execute_host(pinned, a, h_out, stream)
+                    t1.record(stream)
+                    torch.cuda.synchronize()
+                    hms = t0.elapsed_time(t1) / reps
+                    line["ghz_with_copies"] = a * n / (hms * 1e-3) / 1e9
+                print(json.dumps(line), flush=True)
+                del d_in
+            plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,8 +510,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the tensor-core and two-kernel comparison runs")
-    ap.add_argument("--config", choices=["c2", "c5"], default="c2",
-                    help="c2: the 32768-channel PFB dump (default); c5: the batched multi-beam workload")
+    ap.add_argument("--sweep", action="store_true",
+                    help="bandwidth against FFT length and accumulation length (Fig. 3 shape)")
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: the 32768-channel PFB dump (default); c1, c3, c4: the other single-bank "
+                         "workloads; c5: the batched multi-beam workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -450,6 +523,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
         return
     if args.config == "c5":
         if rank == 0:

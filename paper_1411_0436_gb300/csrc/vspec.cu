@@ -81,6 +81,8 @@ std::vector<Pass> make_passes(int L, const std::vector<int> &radices, int *tw_en
         p.lb = lb;
         p.m = lb / r;
         p.off = off;
+        p.lr = ilog2(r);
+        p.lm = ilog2(p.m);
         off += p.m * (r - 1);
         ps.push_back(p);
         lb /= r;
@@ -759,6 +761,8 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     ca.N2 = p->N2;
     ca.C = p->C;
     ca.P = p->P;
+    ca.lC = ilog2(p->C);
+    ca.lN2 = ilog2(p->N2);
     ca.npass = (int)p->passA.size();
     for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
 
@@ -771,6 +775,8 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     cb.N1 = p->N1;
     cb.N2 = p->N2;
     cb.RB = p->RB;
+    cb.lN1 = ilog2(p->N1);
+    cb.lRB = ilog2(p->RB);
     cb.npass = (int)p->passB.size();
     for (int i = 0; i < cb.npass; i++) cb.pass[i] = p->passB[i];
     cb.groups = p->groups_b;
@@ -1068,6 +1074,8 @@ vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
             ps[i].lb = lb;
             ps[i].m = lb / r;
             ps[i].off = off;
+            ps[i].lr = ilog2(r);
+            ps[i].lm = ilog2(lb / r);
             off += ps[i].m * (r - 1);
             lb /= r;
         }
@@ -1185,6 +1193,8 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     ca.N2 = c.N2;
     ca.C = c.C;
     ca.P = c.P;
+    ca.lC = ilog2(c.C);
+    ca.lN2 = ilog2(c.N2);
     ca.npass = c.nA;
     for (int i = 0; i < c.nA; i++) ca.pass[i] = c.passA[i];
     vspec::RowParams cb;
@@ -1195,6 +1205,8 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     cb.N1 = c.N1;
     cb.N2 = c.N2;
     cb.RB = c.RB;
+    cb.lN1 = ilog2(c.N1);
+    cb.lRB = ilog2(c.RB);
     cb.npass = c.nB;
     for (int i = 0; i < c.nB; i++) cb.pass[i] = c.passB[i];
     cb.groups = c.groups_b;

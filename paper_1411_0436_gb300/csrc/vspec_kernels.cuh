@@ -46,6 +46,7 @@ struct ColParams {
     const float2 *twZ;   // [pos][n1]: W_N^(n1 * k2(pos)) (rows in pass-output order)
     void *Z;             // chunk scratch [s_local][pos][n1] of Elem::T
     int N, N1, N2, C, P, npass;
+    int lC, lN2;         // log2 C, log2 N2
     Pass pass[kMaxPasses];
     long long s0;        // absolute index of the chunk's first spectrum
     int sc;              // spectra in this chunk
@@ -58,6 +59,7 @@ struct RowParams {
     void *partial_comp;  // Kahan compensation of `partial` (compensated plans only)
     const float2 *twB;   // per-pass twiddles of the length-N1 row DFTs
     int N, N1, N2, RB, npass;
+    int lN1, lRB;        // log2 N1, log2 RB
     Pass pass[kMaxPasses];
     int sc, groups;
 };
@@ -119,7 +121,7 @@ __device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<
     const int n1_0 = blockIdx.x * C;
     if (p.npass == 0) {  // N2 == 1: the pre-filter output is the row itself
         for (int u = threadIdx.x; u < nb * C; u += blockDim.x) {
-            const int sb = u / C, c = u - sb * C;
+            const int sb = u >> p.lC, c = u & (C - 1);
             T *Zs = reinterpret_cast<T *>(p.Z) + (size_t)(s_local0 + sb) * p.N;
             Zs[n1_0 + c] = data[u];
         }
@@ -127,11 +129,11 @@ __device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<
     for (int ip = 0; ip < p.npass; ip++) {
         const Pass ps = p.pass[ip];
         const bool last = ip == p.npass - 1;
-        const int per = C * (N2 / ps.r);  // butterflies per spectrum
-        for (int u = threadIdx.x; u < nb * per; u += blockDim.x) {
-            const int sb = u / per, w = u - sb * per;
-            const int c = w & (C - 1), bj = w / C;
-            const int b = bj / ps.m, j = bj - b * ps.m;
+        const int lper = p.lC + p.lN2 - ps.lr;  // log2 of the butterflies per spectrum
+        for (int u = threadIdx.x; u < (nb << lper); u += blockDim.x) {
+            const int sb = u >> lper, w = u & ((1 << lper) - 1);
+            const int c = w & (C - 1), bj = w >> p.lC;
+            const int b = bj >> ps.lm, j = bj & (ps.m - 1);
             T *d = data + sb * pts;
             T *Zs = reinterpret_cast<T *>(p.Z) + (size_t)(s_local0 + sb) * p.N;
             if (ps.r == 2) col_butterfly<2, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
         const int idx = threadIdx.x + i * blockDim.x;  // = n2 * C + c
-        const int c = idx & (C - 1), n2 = idx / C;
+        const int c = idx & (C - 1), n2 = idx >> p.lC;
         n_pt[i] = n1_0 + c + (long long)p.N1 * n2;
         sm_pt[i] = idx;
 #pragma unroll
@@ -317,8 +319,9 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<
         for (int q = 0; q < R; q++) row[pad16(base + q * ps.m)] = v[q];
     } else {
         // m == 1: output q of unit (r, b); accumulator slot q * U + (r * N1/R + b)
-        const int U = p.RB * (p.N1 / R);
-        const int w = r * (p.N1 / R) + b;
+        constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+        const int U = p.RB << (p.lN1 - LR);
+        const int w = (r << (p.lN1 - LR)) + b;
 #pragma unroll
         for (int q = 0; q < R; q++) {
             if constexpr (KAHAN) {
@@ -360,11 +363,11 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
         for (int ip = 0; ip < p.npass; ip++) {
             const Pass ps = p.pass[ip];
             const bool first = ip == 0, last = ip == p.npass - 1;
-            const int per_row = p.N1 / ps.r;
-            const int nb = p.RB * per_row;
+            const int lper = p.lN1 - ps.lr;  // log2 butterflies per row
+            const int nb = p.RB << lper;
             for (int u = threadIdx.x; u < nb; u += blockDim.x) {
-                const int r = u / per_row, w = u - r * per_row;
-                const int b = w / ps.m, j = w - b * ps.m;
+                const int r = u >> lper, w = u & ((1 << lper) - 1);
+                const int b = w >> ps.lm, j = w & (ps.m - 1);
                 switch (ps.r) {
                     case 2: row_butterfly<2, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
                     case 4: row_butterfly<4, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
@@ -378,11 +381,12 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
 
     // flush: accumulator slot e = q * U + (r * N1/R + b) holds row r, position b*R + q
     const int RL = p.pass[p.npass - 1].r;
-    const int U = p.RB * (p.N1 / RL);
+    const int lq = p.lN1 - p.pass[p.npass - 1].lr;  // log2 (N1 / RL)
+    const int lU = p.lRB + lq;
     A *part = reinterpret_cast<A *>(p.partial) + (size_t)g * p.N;
     for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
-        const int q = e / U, w = e - q * U;
-        const int r = w / (p.N1 / RL), b = w - r * (p.N1 / RL);
+        const int q = e >> lU, w = e & ((1 << lU) - 1);
+        const int r = w >> lq, b = w & ((1 << lq) - 1);
         const size_t o = (size_t)(blockIdx.x * p.RB + r) * p.N1 + b * RL + q;
         if constexpr (KAHAN) {
             A *pc = reinterpret_cast<A *>(p.partial_comp) + (size_t)g * p.N;

@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
         for (int ip = 1; ip < p.npass; ip++) {
             const Pass ps = p.pass[ip];
             const bool last = ip == p.npass - 1;
-            const int per_row = kTcN1 / ps.r;
+            const int per_row = kTcN1 >> ps.lr;
             for (int u = tid; u < per_row; u += blockDim.x) {
-                const int b = u / ps.m, jj = u - b * ps.m;
+                const int b = u >> ps.lm, jj = u & (ps.m - 1);
                 switch (ps.r) {
                     case 2: row_butterfly<2, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
                     case 4: row_butterfly<4, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
 
     // flush: accumulator slot e = q * U + b holds position b * RL + q
     const int RL = p.pass[p.npass - 1].r;
-    const int U = kTcN1 / RL;
+    const int U = kTcN1 >> p.pass[p.npass - 1].lr;
     float4 *part = reinterpret_cast<float4 *>(p.partial) + (size_t)g * p.N + (size_t)blockIdx.x * kTcN1;
     for (int e = tid; e < kTcN1; e += blockDim.x) {
-        const int q = e / U, b = e - q * U;
+        const int q = e >> (11 - p.pass[p.npass - 1].lr), b = e & (U - 1);
         float4 a = part[b * RL + q];
         if constexpr (KAHAN) {
             float4 *pc = reinterpret_cast<float4 *>(p.partial_comp) + (size_t)g * p.N + (size_t)blockIdx.x * kTcN1;

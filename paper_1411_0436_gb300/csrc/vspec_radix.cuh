@@ -119,6 +119,8 @@ struct Pass {
     int m;
     int lb;
     int off;
+    int lr;  // log2 r
+    int lm;  // log2 m
 };
 
 }  // namespace vspec
