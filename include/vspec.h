@@ -185,10 +185,12 @@ VSPEC_API vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out
 
 /*
  * Plan properties: bytes of device scratch the plan owns (coefficients,
- * twiddles and intermediate buffers) and the number of passes the design makes
- * over the int8 input in HBM per execute (1: every input byte is fetched from
- * HBM once; overlapping PFB frames are re-read from on-chip storage or L2).
- * Either output pointer may be NULL.
+ * twiddles and intermediate buffers) and the number of HBM passes the design
+ * makes per execute: 1 when every input byte is fetched from HBM once and
+ * everything else stays on chip or in L2 (overlapping PFB frames are re-read
+ * from on-chip storage or L2); 2 when, in addition, the two-kernel path's
+ * chunk scratch (complex FP32 per channel and spectrum) is larger than half
+ * the L2 and makes a round trip through HBM. Either output pointer may be NULL.
  */
 VSPEC_API vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int *hbm_passes);
 
@@ -211,6 +213,50 @@ VSPEC_API vspec_status vspec_plan_set_profiling(vspec_plan *plan, int enable);
 VSPEC_API vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset,
                                                const char **name, long long *launches,
                                                long long *spectra, double *total_ms);
+
+/*
+ * Launch shape of a plan. The results do not depend on it beyond FP32
+ * summation order.
+ *
+ * Two-kernel plans (every plan except the one-pass fused one) run the
+ * four-step FFT through a chunk scratch. A chunk is a run of spectra whose
+ * column DFTs (kernel A) all finish before their row DFTs (kernel B) start.
+ * Each launch splits its (tile, spectrum) items evenly over its CTAs; a CTA
+ * that starts a run of a column tile re-reads ntaps-1 frames to fill its FIR
+ * window, and each CTA of kernel B keeps its row tile's sums in a partial-sum
+ * slot that is folded into d_accum once per execute.
+ *   chunk_spectra    1 .. limit.chunk_spectra (a chunk longer than the plan's
+ *                    scratch holds grows the scratch: the call then
+ *                    synchronises the device and allocates)
+ *   blocks_a         CTAs per kernel-A launch: 0 (one wave, the default) or
+ *                    1 .. limit.blocks_a
+ *   blocks_b         CTAs per kernel-B launch: 0 (one wave) or 1 .. limit.blocks_b
+ *   assist_permille  0
+ * One-pass fused plans (dual-pol, 2048..32768 channels) run clusters of CTAs,
+ * and a device whose SM count is not a multiple of the cluster size leaves
+ * SMs idle. Such a plan owns a two-kernel plan that channelizes the last
+ * assist_permille thousandths of every execute's spectra on a second stream,
+ * concurrently with the clusters (none if that share is under 32 spectra).
+ *   chunk_spectra, blocks_a, blocks_b  0
+ *   assist_permille  0 (no assist) .. limit.assist_permille (0 where the
+ *                    device leaves no SMs idle); the default balances the
+ *                    two paths' measured per-SM rates
+ * vspec_plan_get_tuning fills the current shape and the limits (either
+ * pointer may be NULL). vspec_plan_set_tuning takes effect at the next
+ * execute; do not call it while an execute of the plan is in flight or being
+ * captured. Errors: VSPEC_ERR_INVALID_ARG (NULL, or a value out of range),
+ * VSPEC_ERR_OOM, VSPEC_ERR_CUDA (growing the scratch).
+ */
+typedef struct {
+    int chunk_spectra;
+    int blocks_a;
+    int blocks_b;
+    int assist_permille;
+} vspec_tuning;
+
+VSPEC_API vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tuning *current,
+                                             vspec_tuning *limit);
+VSPEC_API vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *tuning);
 
 /*
  * Allocation-free variant of vspec_execute. The paper has no counterpart: it

@@ -116,7 +116,10 @@ struct vspec_plan {
     int N = 0, P = 0, npol = 0, mode = 0, window = 0, device = 0;
     int N1 = 0, N2 = 0, C = 0, PT = 0, PPT = 0, TA = 0, RB = 0, TB = 0;
     int num_sms = 0, occA = 1, occB = 1;
-    int sc_max = 1, groups_b = 1;
+    int sc_max = 1;                  // spectra per chunk
+    int sc_cap = 1, slots_cap = 1;   // largest chunk a tuning may ask for; slots allocated
+    int sc_alloc = 1;                // chunk spectra the scratch holds now
+    int blocks_a = 0, blocks_b = 0;  // CTAs per kernel-A / kernel-B launch, 0: one wave
     size_t smemA = 0, smemB = 0;
     std::vector<Pass> passA, passB;
     float *coef = nullptr;
@@ -131,6 +134,14 @@ struct vspec_plan {
     size_t smemF = 0;
     const void *kernelF = nullptr;
     unsigned flags = 0;
+    // fused plans: a two-kernel plan that channelizes a share of the spectra
+    // on the SMs the clusters leave idle, concurrently with the fused kernel
+    vspec_plan *assist = nullptr;
+    vspec_plan *owner = nullptr;  // the plan whose profiling records this plan's launches
+    int assist_permille = 0;
+    int prio_high = 0;            // greatest stream priority of the device
+    cudaStream_t assist_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_main = nullptr, ev_assist = nullptr;
     bool tc = false;           // first row pass on the tensor cores
     bool kahan = false;        // compensated accumulation at every level
     void *partial_comp = nullptr, *out_comp = nullptr;
@@ -200,40 +211,45 @@ cudaError_t take_event(vspec_plan *p, cudaEvent_t *ev) {
 // profiling mode bracket it with events.
 vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 grid, dim3 block,
                     void **args, size_t smem, cudaStream_t st, int cluster = 0) {
+    vspec_plan *o = p->owner ? p->owner : p;  // an assist plan records into its owner
     vspec_plan::Rec r{kind, spectra, nullptr, nullptr};
-    if (p->profiling) {
-        VSPEC_CUDA(take_event(p, &r.start));
-        VSPEC_CUDA(take_event(p, &r.stop));
+    if (o->profiling) {
+        VSPEC_CUDA(take_event(o, &r.start));
+        VSPEC_CUDA(take_event(o, &r.stop));
         VSPEC_CUDA(cudaEventRecord(r.start, st));
     }
     cudaError_t e;
     if (cluster > 0) {
+        // cluster launches go first: the highest priority places the clusters
+        // before any concurrent assist CTA takes an SM they need
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
         cfg.blockDim = block;
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = cluster;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributePriority;
+        attr[1].val.priority = p->prio_high;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         e = cudaLaunchKernelExC(&cfg, fn, args);
     } else {
         e = cudaLaunchKernel(fn, grid, block, args, smem, st);
     }
     if (e != cudaSuccess) {
-        if (p->profiling) {
-            p->event_pool.push_back(r.start);
-            p->event_pool.push_back(r.stop);
+        if (o->profiling) {
+            o->event_pool.push_back(r.start);
+            o->event_pool.push_back(r.stop);
         }
         return cuda_fail(e, kKindNames[kind]);
     }
-    if (p->profiling) {
+    if (o->profiling) {
         VSPEC_CUDA(cudaEventRecord(r.stop, st));
-        p->recs.push_back(r);
+        o->recs.push_back(r);
     }
     return VSPEC_OK;
 }
@@ -258,6 +274,13 @@ const void *pick_kernel_fused(int logn1, int pt) {
 void free_plan(vspec_plan *p) {
     if (!p) return;
     release_records(p);
+    if (p->assist) {
+        free_plan(p->assist);
+        cudaStreamDestroy(p->assist_st);
+        cudaEventDestroy(p->ev_fork);
+        cudaEventDestroy(p->ev_main);
+        cudaEventDestroy(p->ev_assist);
+    }
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
     if (p->host_ready) {
         cudaStreamDestroy(p->copy_st);
@@ -299,8 +322,18 @@ vspec_status dev_alloc(void **ptr, size_t bytes, size_t *total) {
     return VSPEC_OK;
 }
 
-// Chunk scratch budget: the per-chunk intermediate stays resident in L2.
-constexpr size_t kScratchBudget = 32u << 20;
+// Chunk scratch: long chunks amortise the per-chunk costs (the FIR window's
+// leading frames, the last partly filled wave of CTAs); the intermediate's
+// HBM round trip costs less than those at this budget (measured on GB300).
+// A tuned chunk may grow the scratch up to kScratchCap.
+constexpr size_t kScratchBudget = 512u << 20;
+constexpr size_t kScratchCap = 2048ull << 20;
+constexpr int kMaxChunkSpectra = 8192;  // small nchan: a default chunk long enough
+constexpr int kMaxWaves = 4;    // largest tuned launch, in waves of CTAs
+
+// Partial-sum slots a kernel-B launch of n CTAs uses: a CTA's rank among the
+// CTAs that share a row tile stays below n / tiles + 2 (span_slot).
+int slots_for(const vspec_plan *p, int n) { return n / (p->N2 / p->RB) + 2; }
 constexpr int kRowElems = 2048;  // target row-DFT elements per kernel-B CTA
 
 // Fused one-pass plan: dual-pol, 2048..32768 channels, 8-tap PFB or direct.
@@ -371,7 +404,6 @@ vspec_status build_fused_plan(vspec_plan *p) {
     if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
     if ((st = dev_alloc(&p->partial, (size_t)p->nclusters * N * sizeof(float4), &tot))) return st;
     p->scratch_bytes = tot;
-    p->groups_b = p->nclusters;
 
     const std::vector<int> kA = digit_reverse(N2, rA), kB = digit_reverse(N1, rB);
     std::vector<int> invA(N2), invB(N1);
@@ -421,7 +453,11 @@ vspec_status build_plan(vspec_plan *p) {
         g_last_error = "nchan too large for this mode in this build";
         return VSPEC_ERR_UNSUPPORTED;
     }
-    int C = std::max(cmin, 256 / N2);
+    // column tile: without a FIR window in registers, enough points per CTA
+    // that every thread holds eight (loads in flight); with one, the window's
+    // registers allow one or two
+    const int pts_target = PT == 1 ? 4096 : 512;
+    int C = std::max(cmin, pts_target / N2);
     C = std::min(C, N1);
     const int pts = N2 * C;
     const int TA = std::min(512, pts);
@@ -496,10 +532,11 @@ vspec_status build_plan(vspec_plan *p) {
         return VSPEC_ERR_UNSUPPORTED;
     }
 
-    p->sc_max = (int)std::max<size_t>(1, kScratchBudget / ((size_t)N * elem));
-    const int blocksB = N2 / p->RB;
-    const int targetB = p->num_sms * p->occB;
-    p->groups_b = std::max(1, std::min(p->sc_max, (targetB + blocksB - 1) / blocksB));
+    const size_t per_spec = (size_t)N * elem;
+    p->sc_cap = (int)std::max<size_t>(1, kScratchCap / per_spec);
+    p->sc_max = std::min({p->sc_cap, kMaxChunkSpectra, (int)std::max<size_t>(1, kScratchBudget / per_spec)});
+    // partial-sum slots for the largest kernel-B launch a tuning may ask for
+    p->slots_cap = slots_for(p, kMaxWaves * p->num_sms * p->occB);
 
     // device tables and scratch
     vspec_status st;
@@ -511,14 +548,15 @@ vspec_status build_plan(vspec_plan *p) {
     if ((st = dev_alloc((void **)&p->twZ, sizeof(float2) * (size_t)N, &tot))) return st;
     if ((st = dev_alloc((void **)&p->invA, sizeof(int) * (size_t)N2, &tot))) return st;
     if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
-    if ((st = dev_alloc(&p->Z, (size_t)p->sc_max * N * elem, &tot))) return st;
-    if ((st = dev_alloc(&p->partial, (size_t)p->groups_b * N * accel, &tot))) return st;
+    p->sc_alloc = p->sc_max;
+    if ((st = dev_alloc(&p->Z, (size_t)p->sc_alloc * N * elem, &tot))) return st;
+    if ((st = dev_alloc(&p->partial, (size_t)p->slots_cap * N * accel, &tot))) return st;
     if (p->tc) {
         if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
         VSPEC_CUDA(cudaMemset(p->tc_status, 0, sizeof(int)));
     }
     if (p->kahan) {
-        if ((st = dev_alloc(&p->partial_comp, (size_t)p->groups_b * N * accel, &tot))) return st;
+        if ((st = dev_alloc(&p->partial_comp, (size_t)p->slots_cap * N * accel, &tot))) return st;
         if ((st = dev_alloc(&p->out_comp, (size_t)N * accel, &tot))) return st;
         VSPEC_CUDA(cudaMemset(p->out_comp, 0, (size_t)N * accel));
     }
@@ -579,6 +617,40 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
     return vspec_plan_create_ex(out, nchan, ntaps, npol, mode, window, 0u);
 }
 
+// Fused plans on a device whose SM count is not a multiple of the cluster
+// size: a two-kernel plan channelizes a share of every execute's spectra on
+// the idle SMs. The share balances the two finishing times: idle SMs at the
+// two-kernel path's per-SM rate against the clusters' SMs at the fused
+// kernel's (tuned on GB300 with 1000-spectrum dumps of 32768 channels: about
+// 0.62 of it with an 8-tap PFB, 0.70 in direct mode). With only a few idle SMs
+// the second path's fixed cost outweighs them.
+constexpr double kAssistPerSmRate = 0.62;        // PFB
+constexpr double kAssistPerSmRateDirect = 0.70;  // direct FFT
+constexpr int kAssistMinSms = 24;      // fewer idle SMs: no assist
+constexpr int kAssistMinSpectra = 32;  // smallest share worth a second path
+constexpr int kAssistMaxPermille = 900;
+
+static vspec_status setup_assist(vspec_plan *p) {
+    VSPEC_CUDA(cudaDeviceGetStreamPriorityRange(nullptr, &p->prio_high));
+    const int busy = p->cluster * p->nclusters;
+    const int idle = p->num_sms - busy;
+    if (idle < kAssistMinSms) return VSPEC_OK;
+    vspec_plan *a = nullptr;
+    vspec_status st = vspec_plan_create_ex(&a, p->N, p->mode == VSPEC_PFB ? p->P : 1, p->npol,
+                                           (vspec_mode)p->mode, (vspec_window)p->window, VSPEC_PLAN_TWO_KERNEL);
+    if (st != VSPEC_OK) return st;
+    a->owner = p;
+    p->assist = a;
+    p->scratch_bytes += a->scratch_bytes;
+    const double w = idle * (p->mode == VSPEC_PFB ? kAssistPerSmRate : kAssistPerSmRateDirect);
+    p->assist_permille = (int)(1000.0 * w / (w + busy) + 0.5);
+    VSPEC_CUDA(cudaStreamCreateWithFlags(&p->assist_st, cudaStreamNonBlocking));
+    VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_main, cudaEventDisableTiming));
+    VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_assist, cudaEventDisableTiming));
+    return VSPEC_OK;
+}
+
 vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
                                   vspec_window window, unsigned flags) {
     if (!out) return VSPEC_ERR_INVALID_ARG;
@@ -605,6 +677,7 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
     }
     p->flags = flags;
     vspec_status st = build_plan(p);
+    if (st == VSPEC_OK && p->fused) st = setup_assist(p);
     if (st != VSPEC_OK) {
         free_plan(p);
         return st;
@@ -648,7 +721,64 @@ vspec_status vspec_plan_destroy(vspec_plan *plan) {
 vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int *hbm_passes) {
     if (!plan) return VSPEC_ERR_INVALID_ARG;
     if (scratch_bytes) *scratch_bytes = plan->scratch_bytes;
-    if (hbm_passes) *hbm_passes = 1;
+    if (hbm_passes) {
+        // the input is read once; the two-kernel path's chunk scratch adds a
+        // write and a read of the intermediate when it cannot stay in L2
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, plan->device) != cudaSuccess) l2 = 0;
+        const size_t zb = (size_t)plan->sc_max * plan->N * (plan->npol == 2 ? sizeof(float4) : sizeof(float2));
+        *hbm_passes = (!plan->fused && zb > (size_t)l2 / 2) ? 2 : 1;
+    }
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tuning *current, vspec_tuning *limit) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (plan->fused) {
+        if (current) *current = vspec_tuning{0, 0, 0, plan->assist ? plan->assist_permille : 0};
+        if (limit) *limit = vspec_tuning{0, 0, 0, plan->assist ? kAssistMaxPermille : 0};
+        return VSPEC_OK;
+    }
+    const int wa = plan->num_sms * plan->occA, wb = plan->num_sms * plan->occB;
+    if (current) *current = vspec_tuning{plan->sc_max, plan->blocks_a, plan->blocks_b, 0};
+    if (limit) *limit = vspec_tuning{plan->sc_cap, kMaxWaves * wa, kMaxWaves * wb, 0};
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
+    if (!plan || !t) return VSPEC_ERR_INVALID_ARG;
+    if (plan->fused) {
+        const int lim = plan->assist ? kAssistMaxPermille : 0;
+        if (t->chunk_spectra != 0 || t->blocks_a != 0 || t->blocks_b != 0 || t->assist_permille < 0 ||
+            t->assist_permille > lim) {
+            g_last_error = "tuning value out of range for a one-pass fused plan";
+            return VSPEC_ERR_INVALID_ARG;
+        }
+        plan->assist_permille = t->assist_permille;
+        return VSPEC_OK;
+    }
+    if (t->chunk_spectra < 1 || t->chunk_spectra > plan->sc_cap || t->blocks_a < 0 ||
+        t->blocks_a > kMaxWaves * plan->num_sms * plan->occA || t->blocks_b < 0 ||
+        t->blocks_b > kMaxWaves * plan->num_sms * plan->occB || t->assist_permille != 0) {
+        g_last_error = "tuning value out of range";
+        return VSPEC_ERR_INVALID_ARG;
+    }
+    if (t->chunk_spectra > plan->sc_alloc) {  // grow the chunk scratch
+        const size_t elem = plan->npol == 2 ? sizeof(float4) : sizeof(float2);
+        const size_t old_bytes = (size_t)plan->sc_alloc * plan->N * elem;
+        void *z = nullptr;
+        size_t tot = 0;
+        VSPEC_CUDA(cudaDeviceSynchronize());
+        vspec_status st = dev_alloc(&z, (size_t)t->chunk_spectra * plan->N * elem, &tot);
+        if (st != VSPEC_OK) return st;
+        cudaFree(plan->Z);
+        plan->Z = z;
+        plan->scratch_bytes += tot - old_bytes;
+        plan->sc_alloc = t->chunk_spectra;
+    }
+    plan->sc_max = t->chunk_spectra;
+    plan->blocks_a = t->blocks_a;
+    plan->blocks_b = t->blocks_b;
     return VSPEC_OK;
 }
 
@@ -692,10 +822,10 @@ vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, f
     return VSPEC_OK;
 }
 
-static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
-                                cudaStream_t st) {
-    vspec_plan *p = plan;
-    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+// One-pass fused path: the cluster kernel over all spectra, then the fold of
+// its per-cluster partial sums into d_accum.
+static vspec_status run_fused(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
+                              cudaStream_t st) {
 
     if (p->fused_w) {
         vspec::fusedw::Params wp;
@@ -742,13 +872,26 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
         void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
         return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
     }
+    return VSPEC_OK;
+}
 
-    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->groups_b * p->N * accel, st));
-    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)p->groups_b * p->N * accel, st));
+// Two-kernel path: chunks of column passes (kernel A) and row passes with
+// detection (kernel B) through the L2-resident scratch, then the fold of the
+// partial sums into d_accum, after `before_fold` if it is given.
+static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
+                                   cudaStream_t st, cudaEvent_t before_fold) {
+    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+    // one full wave of CTAs per launch unless tuned; the work is split evenly
+    // over them (block_span), so every SM stays busy to the end of a launch
+    const int nA = p->blocks_a > 0 ? p->blocks_a : p->num_sms * p->occA;
+    const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
+    const int slots = slots_for(p, nB);
+    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
+    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
 
-    const int sc_full = std::min(nspectra, p->sc_max);
-    const int blocksA = p->N1 / p->C;
-    const int targetA = p->num_sms * p->occA;
+    // equal chunks of at most sc_max spectra (no short ragged last chunk)
+    const int nchunks = (nspectra + p->sc_max - 1) / p->sc_max;
+    const int sc_full = (nspectra + nchunks - 1) / nchunks;
 
     vspec::ColParams ca;
     ca.in = d_in;
@@ -765,6 +908,7 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     ca.lN2 = ilog2(p->N2);
     ca.npass = (int)p->passA.size();
     for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
+    ca.tiles = p->N1 / p->C;
 
     vspec::RowParams cb;
     cb.Z = p->Z;
@@ -779,43 +923,60 @@ static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspect
     cb.lRB = ilog2(p->RB);
     cb.npass = (int)p->passB.size();
     for (int i = 0; i < cb.npass; i++) cb.pass[i] = p->passB[i];
-    cb.groups = p->groups_b;
+    cb.tiles = p->N2 / p->RB;
+    cb.slots = slots;
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);
-        int ga = (targetA + blocksA - 1) / blocksA;
-        ga = std::max(1, std::min(ga, sc));
         ca.s0 = s0;
         ca.sc = sc;
-        ca.groups = ga;
         void *argsA[] = {&ca};
-        vspec_status r = launch(p, 0, sc, p->kernelA, dim3(blocksA, ga), dim3(p->TA), argsA, p->smemA, st);
+        // no more CTAs than items: every block then has work
+        const int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
+        vspec_status r = launch(p, 0, sc, p->kernelA, dim3(ga), dim3(p->TA), argsA, p->smemA, st);
         if (r != VSPEC_OK) return r;
         cb.sc = sc;
         vspec::TcStatus ts{p->tc_status};
         void *argsB[] = {&cb, &ts};
-        r = launch(p, 1, sc, p->kernelB, dim3(p->N2 / p->RB, p->groups_b), dim3(p->TB), argsB, p->smemB, st);
+        const int gb = (int)std::min<long long>(nB, (long long)cb.tiles * sc);
+        r = launch(p, 1, sc, p->kernelB, dim3(gb), dim3(p->TB), argsB, p->smemB, st);
         if (r != VSPEC_OK) return r;
     }
+    if (before_fold) VSPEC_CUDA(cudaStreamWaitEvent(st, before_fold, 0));
     if (p->kahan) {
         const void *part = p->partial, *pcomp = p->partial_comp;
-        int groups = p->groups_b, N = p->N, N1 = p->N1, N2 = p->N2;
+        int groups = slots, N = p->N, N1 = p->N1, N2 = p->N2;
         const int *ia = p->invA, *ib = p->invB;
         void *outp = d_accum, *ocomp = p->out_comp;
         void *argsR[] = {&part, &pcomp, &groups, &N, &N1, &N2, &ia, &ib, &outp, &ocomp};
-        vspec_status r = launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
-        if (r != VSPEC_OK) return r;
-        return VSPEC_OK;
+        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
     }
-    {
-        const void *part = p->partial;
-        int groups = p->groups_b, N = p->N, N1 = p->N1, N2 = p->N2;
-        const int *ia = p->invA, *ib = p->invB;
-        void *outp = d_accum;
-        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
-        vspec_status r = launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
-        if (r != VSPEC_OK) return r;
-    }
+    const void *part = p->partial;
+    int groups = slots, N = p->N, N1 = p->N1, N2 = p->N2;
+    const int *ia = p->invA, *ib = p->invB;
+    void *outp = d_accum;
+    void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
+    return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+}
+
+static vspec_status execute_one(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
+                                cudaStream_t st) {
+    if (!p->fused) return run_two_kernel(p, d_in, nspectra, d_accum, st, nullptr);
+    const int sa = p->assist ? (int)((long long)nspectra * p->assist_permille / 1000) : 0;
+    if (sa < kAssistMinSpectra) return run_fused(p, d_in, nspectra, d_accum, st);
+    // fused kernel on `st` over the first spectra, the assist plan on its own
+    // stream over the rest; the two folds into d_accum are ordered
+    const int sf = nspectra - sa;
+    VSPEC_CUDA(cudaEventRecord(p->ev_fork, st));
+    VSPEC_CUDA(cudaStreamWaitEvent(p->assist_st, p->ev_fork, 0));
+    vspec_status r = run_fused(p, d_in, sf, d_accum, st);
+    if (r != VSPEC_OK) return r;
+    VSPEC_CUDA(cudaEventRecord(p->ev_main, st));
+    r = run_two_kernel(p->assist, d_in + (size_t)sf * p->N * p->npol * 2, sa, d_accum, p->assist_st,
+                       p->ev_main);
+    if (r != VSPEC_OK) return r;
+    VSPEC_CUDA(cudaEventRecord(p->ev_assist, p->assist_st));
+    VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_assist, 0));
     return VSPEC_OK;
 }
 
@@ -968,7 +1129,7 @@ namespace {
 
 constexpr int kNoAllocMaxChan = 32768;  // largest nchan the fixed array holds
 constexpr int kNoAllocChunk = 16;       // spectra per scratch chunk
-constexpr int kNoAllocGroups = 16;      // kernel-B spectrum groups
+constexpr int kNoAllocGroups = 16;      // kernel-B partial-sum slots
 constexpr int kMaxDevices = 64;
 
 // byte offsets inside the array (every region 256-byte aligned)
@@ -989,7 +1150,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 struct NoAllocCfg {
     int N, P, npol, mode, window;
-    int N1, N2, C, PT, PPT, TA, RB, TB, groups_b, sc_max, occA;
+    int N1, N2, C, PT, PPT, TA, RB, TB, sc_max, occA;
+    int blocks_a, blocks_b, slots;  // CTAs per launch; partial-sum slots
     int nA, nB;
     Pass passA[vspec::kMaxPasses], passB[vspec::kMaxPasses];
     const void *kA, *kB, *kR;
@@ -1097,9 +1259,11 @@ vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occA, c->kA, c->TA, c->smemA));
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, c->kB, c->TB, c->smemB));
     c->sc_max = (int)std::min<size_t>(kNoAllocChunk, (size_t)kNoAllocChunk * kNoAllocMaxChan / N);
-    const int blocksB = N2 / c->RB;
-    c->groups_b = std::max(1, std::min(std::min(kNoAllocGroups, c->sc_max),
-                                       (num_sms * std::max(1, occB) + blocksB - 1) / blocksB));
+    // one wave of CTAs per launch, as many kernel-B CTAs as the slots allow
+    const int tilesB = N2 / c->RB;
+    c->blocks_a = num_sms * std::max(1, c->occA);
+    c->blocks_b = std::min(num_sms * std::max(1, occB), (kNoAllocGroups - 2) * tilesB);
+    c->slots = c->blocks_b / tilesB + 2;
     return VSPEC_OK;
 }
 
@@ -1180,7 +1344,7 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
 
     // partial sums must start at zero on every call
     const size_t accel = npol == 2 ? sizeof(float4) : sizeof(float);
-    VSPEC_CUDA(cudaMemsetAsync(partial, 0, (size_t)c.groups_b * c.N * accel, st));
+    VSPEC_CUDA(cudaMemsetAsync(partial, 0, (size_t)c.slots * c.N * accel, st));
 
     vspec::ColParams ca;
     ca.in = d_in;
@@ -1209,25 +1373,25 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     cb.lRB = ilog2(c.RB);
     cb.npass = c.nB;
     for (int i = 0; i < c.nB; i++) cb.pass[i] = c.passB[i];
-    cb.groups = c.groups_b;
+    cb.tiles = c.N2 / c.RB;
+    cb.slots = c.slots;
+    ca.tiles = c.N1 / c.C;
 
-    const int blocksA = c.N1 / c.C;
-    const int targetA = d.num_sms * std::max(1, c.occA);
     const int sc_full = std::min(nspectra, c.sc_max);
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);
-        const int ga = std::max(1, std::min((targetA + blocksA - 1) / blocksA, sc));
         ca.s0 = s0;
         ca.sc = sc;
-        ca.groups = ga;
         void *argsA[] = {&ca};
-        VSPEC_CUDA(cudaLaunchKernel(c.kA, dim3(blocksA, ga), dim3(c.TA), argsA, c.smemA, st));
+        const int ga = (int)std::min<long long>(c.blocks_a, (long long)ca.tiles * sc);
+        VSPEC_CUDA(cudaLaunchKernel(c.kA, dim3(ga), dim3(c.TA), argsA, c.smemA, st));
         cb.sc = sc;
         void *argsB[] = {&cb};
-        VSPEC_CUDA(cudaLaunchKernel(c.kB, dim3(c.N2 / c.RB, c.groups_b), dim3(c.TB), argsB, c.smemB, st));
+        const int gb = (int)std::min<long long>(c.blocks_b, (long long)cb.tiles * sc);
+        VSPEC_CUDA(cudaLaunchKernel(c.kB, dim3(gb), dim3(c.TB), argsB, c.smemB, st));
     }
     const void *part = partial;
-    int groups = c.groups_b, N = c.N, N1 = c.N1, N2 = c.N2;
+    int groups = c.slots, N = c.N, N1 = c.N1, N2 = c.N2;
     const int *ia = invA, *ib = invB;
     void *outp = d_accum;
     void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};

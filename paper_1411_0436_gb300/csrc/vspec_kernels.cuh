@@ -50,7 +50,7 @@ struct ColParams {
     Pass pass[kMaxPasses];
     long long s0;        // absolute index of the chunk's first spectrum
     int sc;              // spectra in this chunk
-    int groups;          // spectrum groups per chunk (gridDim.y)
+    int tiles;           // column tiles, N1 / C
 };
 
 struct RowParams {
@@ -61,8 +61,32 @@ struct RowParams {
     int N, N1, N2, RB, npass;
     int lN1, lRB;        // log2 N1, log2 RB
     Pass pass[kMaxPasses];
-    int sc, groups;
+    int sc;              // spectra in this chunk
+    int tiles;           // row tiles, N2 / RB
+    int slots;           // partial-sum slots (span_slot bound)
 };
+
+// ------------------------------------------------------------ work split --
+// A launch's work is tiles x sc (tile, spectrum) items, tile-major. Block k
+// of n takes items [k T / n, (k+1) T / n), T = tiles * sc: equal shares to
+// within one item, whatever the tile count, so one wave of CTAs is busy to
+// the end. A block's items form at most a few runs of consecutive spectra of
+// one tile (segments).
+struct Span {
+    long long lo, hi;
+};
+__device__ __forceinline__ Span block_span(int tiles, int sc) {
+    const long long T = (long long)tiles * sc;
+    return {T * blockIdx.x / gridDim.x, T * (blockIdx.x + 1) / gridDim.x};
+}
+// Rank of this block among the blocks whose items meet tile x: the first
+// such block is the one holding item x * sc, the largest k with
+// floor(k T / n) <= x * sc. Ranks are below n / tiles + 2.
+__device__ __forceinline__ int span_slot(int tiles, int sc, int x) {
+    const long long T = (long long)tiles * sc;
+    const long long k_lo = (((long long)x * sc + 1) * gridDim.x - 1) / T;
+    return (int)(blockIdx.x - k_lo);
+}
 
 // ---------------------------------------------------------------- unpack ---
 // Exact int8 -> fp32: placing (b ^ 0x80) in the low mantissa byte of 2^23
@@ -114,11 +138,11 @@ __device__ __forceinline__ void col_butterfly(const ColParams &p, typename Elem<
 // [spectrum][n2][c]), then W_N^(n1 k2) and the store into the chunk scratch.
 template <int NPOL, int RMAX>
 __device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<NPOL>::T *data,
-                                              int s_local0, int nb) {
+                                              int x, int s_local0, int nb) {
     using T = typename Elem<NPOL>::T;
     const int C = p.C, N2 = p.N2;
     const int pts = N2 * C;
-    const int n1_0 = blockIdx.x * C;
+    const int n1_0 = x * C;
     if (p.npass == 0) {  // N2 == 1: the pre-filter output is the row itself
         for (int u = threadIdx.x; u < nb * C; u += blockDim.x) {
             const int sb = u >> p.lC, c = u & (C - 1);
@@ -162,21 +186,15 @@ __host__ __device__ constexpr int col_radix_cap(int npol, int pt, int ppt) {
 // DFTs then run together. The window stays live through the column DFTs, so
 // the widest butterfly is capped by the window's register footprint; the
 // plan builds its pass list with the same cap (col_radix_cap).
+// One segment: spectra [s_beg, s_end) of the chunk for column tile x.
 template <int NPOL, int PT, int PPT>
-__global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__ ColParams p) {
+__device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename Elem<NPOL>::T *data, int x,
+                                                   int s_beg, int s_end) {
     using T = typename Elem<NPOL>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
     constexpr int NC = 2 * NPOL;  // floats per sample
-
-    const int g = blockIdx.y;
-    const int s_beg = (int)((long long)p.sc * g / p.groups);
-    const int s_end = (int)((long long)p.sc * (g + 1) / p.groups);
-    if (s_beg >= s_end) return;
-
     const int C = p.C;
     const int pts = p.N2 * C;
-    const int n1_0 = blockIdx.x * C;
+    const int n1_0 = x * C;
     const int D = PT - p.P;  // leading zero taps
 
     long long n_pt[PPT];
@@ -235,7 +253,23 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
             }
         }
         __syncthreads();
-        col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, s_base, nb);
+        col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, x, s_base, nb);
+    }
+}
+
+template <int NPOL, int PT, int PPT>
+__global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__ ColParams p) {
+    using T = typename Elem<NPOL>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);
+        const long long base = (long long)x * p.sc;
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        // col_fft_store ends on a barrier, so the next segment may reuse data
+        fir_colfft_segment<NPOL, PT, PPT>(p, data, x, (int)(f - base), s_end);
+        f = base + s_end;
     }
 }
 
@@ -291,7 +325,7 @@ __device__ __forceinline__ float4 sub4(float4 a, float4 b) {
 }
 
 template <int R, int NPOL, bool KAHAN = false>
-__device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<NPOL>::T *data,
+__device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::Acc *acc,
                                               const typename Elem<NPOL>::T *Zs, const Pass ps,
                                               bool first, bool last, int r, int b, int j,
@@ -301,7 +335,7 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, typename Elem<
     T *row = data + r * rowstride;
     T v[R];
     if (first) {
-        const T *zr = Zs + (size_t)(blockIdx.x * p.RB + r) * p.N1;
+        const T *zr = Zs + (size_t)(x * p.RB + r) * p.N1;
 #pragma unroll
         for (int q = 0; q < R; q++) v[q] = zr[base + q * ps.m];
     } else {
@@ -344,64 +378,71 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
     T *data = reinterpret_cast<T *>(smem_raw);
     A *acc = reinterpret_cast<A *>(data + p.RB * rowstride);
     A *comp = acc + p.RB * p.N1;  // compensation (compensated plans only)
-
-    const int g = blockIdx.y;
-    const int s_beg = (int)((long long)p.sc * g / p.groups);
-    const int s_end = (int)((long long)p.sc * (g + 1) / p.groups);
-    if (s_beg >= s_end) return;
-
     const int nacc = p.RB * p.N1;
-    for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
-        if constexpr (NPOL == 2) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else acc[e] = 0.f;
-        if constexpr (KAHAN) comp[e] = acc[e];
-    }
-    __syncthreads();
-
-    for (int s = s_beg; s < s_end; s++) {
-        const T *Zs = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
-        for (int ip = 0; ip < p.npass; ip++) {
-            const Pass ps = p.pass[ip];
-            const bool first = ip == 0, last = ip == p.npass - 1;
-            const int lper = p.lN1 - ps.lr;  // log2 butterflies per row
-            const int nb = p.RB << lper;
-            for (int u = threadIdx.x; u < nb; u += blockDim.x) {
-                const int r = u >> lper, w = u & ((1 << lper) - 1);
-                const int b = w >> ps.lm, j = w & (ps.m - 1);
-                switch (ps.r) {
-                    case 2: row_butterfly<2, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                    case 4: row_butterfly<4, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                    case 8: row_butterfly<8, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                    default: row_butterfly<16, NPOL, KAHAN>(p, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                }
-            }
-            __syncthreads();
-        }
-    }
-
-    // flush: accumulator slot e = q * U + (r * N1/R + b) holds row r, position b*R + q
     const int RL = p.pass[p.npass - 1].r;
     const int lq = p.lN1 - p.pass[p.npass - 1].lr;  // log2 (N1 / RL)
     const int lU = p.lRB + lq;
-    A *part = reinterpret_cast<A *>(p.partial) + (size_t)g * p.N;
-    for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
-        const int q = e >> lU, w = e & ((1 << lU) - 1);
-        const int r = w >> lq, b = w & ((1 << lq) - 1);
-        const size_t o = (size_t)(blockIdx.x * p.RB + r) * p.N1 + b * RL + q;
-        if constexpr (KAHAN) {
-            A *pc = reinterpret_cast<A *>(p.partial_comp) + (size_t)g * p.N;
-            A a = part[o], c = pc[o];
-            if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[e], comp[e]));
-            else kahan_add(a, c, acc[e] - comp[e]);
-            part[o] = a;
-            pc[o] = c;
-        } else if constexpr (NPOL == 2) {
-            float4 a = part[o];
-            const float4 d = acc[e];
-            part[o] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
-        } else {
-            part[o] += acc[e];
+
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);  // row tile
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+
+        for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+            if constexpr (NPOL == 2) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else acc[e] = 0.f;
+            if constexpr (KAHAN) comp[e] = acc[e];
         }
+        __syncthreads();
+
+        for (int s = s_beg; s < s_end; s++) {
+            const T *Zs = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
+            for (int ip = 0; ip < p.npass; ip++) {
+                const Pass ps = p.pass[ip];
+                const bool first = ip == 0, last = ip == p.npass - 1;
+                const int lper = p.lN1 - ps.lr;  // log2 butterflies per row
+                const int nb = p.RB << lper;
+                for (int u = threadIdx.x; u < nb; u += blockDim.x) {
+                    const int r = u >> lper, w = u & ((1 << lper) - 1);
+                    const int b = w >> ps.lm, j = w & (ps.m - 1);
+                    switch (ps.r) {
+                        case 2: row_butterfly<2, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                        case 4: row_butterfly<4, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                        case 8: row_butterfly<8, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                        default: row_butterfly<16, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+
+        // flush into this block's slot: accumulator slot e = q * U + (r * N1/R + b)
+        // holds row r, position b*R + q
+        const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N;
+        A *part = reinterpret_cast<A *>(p.partial) + so;
+        for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+            const int q = e >> lU, w = e & ((1 << lU) - 1);
+            const int r = w >> lq, b = w & ((1 << lq) - 1);
+            const size_t o = (size_t)(x * p.RB + r) * p.N1 + b * RL + q;
+            if constexpr (KAHAN) {
+                A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
+                A a = part[o], c = pc[o];
+                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[e], comp[e]));
+                else kahan_add(a, c, acc[e] - comp[e]);
+                part[o] = a;
+                pc[o] = c;
+            } else if constexpr (NPOL == 2) {
+                float4 a = part[o];
+                const float4 d = acc[e];
+                part[o] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+            } else {
+                part[o] += acc[e];
+            }
+        }
+        __syncthreads();  // acc is zeroed again by the next segment
     }
 }
 

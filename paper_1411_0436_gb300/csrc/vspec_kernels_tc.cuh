@@ -40,10 +40,6 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     __shared__ uint32_t tmem_slot;
     __shared__ float2 w16[16];
 
-    const int g = blockIdx.y;
-    const int s_beg = (int)((long long)p.sc * g / p.groups);
-    const int s_end = (int)((long long)p.sc * (g + 1) / p.groups);
-    if (s_beg >= s_end) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -56,10 +52,6 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fill_w16(w16);
-    for (int e = tid; e < kTcN1; e += blockDim.x) {
-        acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (KAHAN) comp[e] = acc[e];
-    }
     __syncthreads();
     stage_dft16_operand(bhi, blo, w16);
     fence_proxy_async();
@@ -70,85 +62,103 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     const Pass p0 = p.pass[0];  // radix 16, block length 2048, 128 butterflies
     bool ok = true;
     uint32_t parity = 0;
-
-    for (int s = s_beg, k = 0; s < s_end && ok; s++, k++) {
-        const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)blockIdx.x * kTcN1;
-        if (tid < kRows) {
-            float2 v0[16], v1[16];
-#pragma unroll
-            for (int r = 0; r < 16; r++) {
-                const float4 e = zr[tid + kRows * r];
-                v0[r] = make_float2(e.x, e.y);
-                v1[r] = make_float2(e.z, e.w);
-            }
-            stage_row(a0hi, a0lo, tid, v0);
-            stage_row(a1hi, a1lo, tid, v1);
-        }
-        fence_proxy_async();
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            issue_dft16(tmem, a0hi, a0lo, bhi, blo, TERMS);
-            issue_dft16(tmem + 32u, a1hi, a1lo, bhi, blo, TERMS);
-            mma_commit(&mbar);
-        }
-        parity = (uint32_t)(k & 1);
-        ok = mbar_wait(&mbar, parity);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok && warp < 4) {
-            float d0[32], d1[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), d0);
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32u, d1);
-            const int j = 32 * warp + lane;
-            const float2 *tw = p.twB + p0.off + j * 15;
-#pragma unroll
-            for (int q = 0; q < 16; q++) {
-                float4 vq = make_float4(d0[2 * q], d0[2 * q + 1], d1[2 * q], d1[2 * q + 1]);
-                if (q > 0) vq = cmul(vq, __ldg(tw + q - 1));
-                data[pad16(j + kRows * q)] = vq;
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(ok);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) break;
-        for (int ip = 1; ip < p.npass; ip++) {
-            const Pass ps = p.pass[ip];
-            const bool last = ip == p.npass - 1;
-            const int per_row = kTcN1 >> ps.lr;
-            for (int u = tid; u < per_row; u += blockDim.x) {
-                const int b = u >> ps.lm, jj = u & (ps.m - 1);
-                switch (ps.r) {
-                    case 2: row_butterfly<2, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
-                    case 4: row_butterfly<4, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
-                    case 8: row_butterfly<8, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
-                    default: row_butterfly<16, 2, KAHAN>(p, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (!ok && tid == 0) atomicExch(ts.status, 1);
-
-    // flush: accumulator slot e = q * U + b holds position b * RL + q
+    int k = 0;  // MMA batches issued so far (mbarrier phase)
     const int RL = p.pass[p.npass - 1].r;
     const int U = kTcN1 >> p.pass[p.npass - 1].lr;
-    float4 *part = reinterpret_cast<float4 *>(p.partial) + (size_t)g * p.N + (size_t)blockIdx.x * kTcN1;
-    for (int e = tid; e < kTcN1; e += blockDim.x) {
-        const int q = e >> (11 - p.pass[p.npass - 1].lr), b = e & (U - 1);
-        float4 a = part[b * RL + q];
-        if constexpr (KAHAN) {
-            float4 *pc = reinterpret_cast<float4 *>(p.partial_comp) + (size_t)g * p.N + (size_t)blockIdx.x * kTcN1;
-            float4 c = pc[b * RL + q];
-            kahan_add(a, c, sub4(acc[e], comp[e]));
-            pc[b * RL + q] = c;
-            part[b * RL + q] = a;
-        } else {
-            const float4 d = acc[e];
-            part[b * RL + q] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi && ok;) {
+        const int x = (int)(f / p.sc);  // row
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        for (int e = tid; e < kTcN1; e += blockDim.x) {
+            acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (KAHAN) comp[e] = acc[e];
         }
+        __syncthreads();
+
+        for (int s = s_beg; s < s_end && ok; s++, k++) {
+            const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)x * kTcN1;
+            if (tid < kRows) {
+                float2 v0[16], v1[16];
+#pragma unroll
+                for (int r = 0; r < 16; r++) {
+                    const float4 e = zr[tid + kRows * r];
+                    v0[r] = make_float2(e.x, e.y);
+                    v1[r] = make_float2(e.z, e.w);
+                }
+                stage_row(a0hi, a0lo, tid, v0);
+                stage_row(a1hi, a1lo, tid, v1);
+            }
+            fence_proxy_async();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                issue_dft16(tmem, a0hi, a0lo, bhi, blo, TERMS);
+                issue_dft16(tmem + 32u, a1hi, a1lo, bhi, blo, TERMS);
+                mma_commit(&mbar);
+            }
+            parity = (uint32_t)(k & 1);
+            ok = mbar_wait(&mbar, parity);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok && warp < 4) {
+                float d0[32], d1[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), d0);
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32u, d1);
+                const int j = 32 * warp + lane;
+                const float2 *tw = p.twB + p0.off + j * 15;
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    float4 vq = make_float4(d0[2 * q], d0[2 * q + 1], d1[2 * q], d1[2 * q + 1]);
+                    if (q > 0) vq = cmul(vq, __ldg(tw + q - 1));
+                    data[pad16(j + kRows * q)] = vq;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            ok = __syncthreads_and(ok);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) break;
+            for (int ip = 1; ip < p.npass; ip++) {
+                const Pass ps = p.pass[ip];
+                const bool last = ip == p.npass - 1;
+                const int per_row = kTcN1 >> ps.lr;
+                for (int u = tid; u < per_row; u += blockDim.x) {
+                    const int b = u >> ps.lm, jj = u & (ps.m - 1);
+                    switch (ps.r) {
+                        case 2: row_butterfly<2, 2, KAHAN>(p, x, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                        case 4: row_butterfly<4, 2, KAHAN>(p, x, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                        case 8: row_butterfly<8, 2, KAHAN>(p, x, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                        default: row_butterfly<16, 2, KAHAN>(p, x, data, acc, nullptr, ps, false, last, 0, b, jj, rowstride, comp); break;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!ok) break;
+
+        // flush into this block's slot: accumulator slot e = q * U + b holds position b * RL + q
+        const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * kTcN1;
+        float4 *part = reinterpret_cast<float4 *>(p.partial) + so;
+        for (int e = tid; e < kTcN1; e += blockDim.x) {
+            const int q = e >> (11 - p.pass[p.npass - 1].lr), b = e & (U - 1);
+            float4 a = part[b * RL + q];
+            if constexpr (KAHAN) {
+                float4 *pc = reinterpret_cast<float4 *>(p.partial_comp) + so;
+                float4 c = pc[b * RL + q];
+                kahan_add(a, c, sub4(acc[e], comp[e]));
+                pc[b * RL + q] = c;
+                part[b * RL + q] = a;
+            } else {
+                const float4 d = acc[e];
+                part[b * RL + q] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+            }
+        }
+        __syncthreads();  // acc is zeroed again by the next segment
     }
+    if (!ok && tid == 0) atomicExch(ts.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {

@@ -53,6 +53,12 @@ def declared_functions() -> list:
     return sorted(set(re.findall(r"\b(vspec_\w+)\s*\(", text)))
 
 
+class VspecTuning(ctypes.Structure):
+    """vspec_tuning: launch shape of the two-kernel path."""
+    _fields_ = [("chunk_spectra", ctypes.c_int), ("blocks_a", ctypes.c_int), ("blocks_b", ctypes.c_int),
+                ("assist_permille", ctypes.c_int)]
+
+
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
     """Load libvspec.so (building it with nvcc first if it is missing)."""
     global _lib
@@ -101,6 +107,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_execute_host.restype = i
         lib.vspec_execute_noalloc.argtypes = [vp, i, i, i, i, i, i, vp, vp]
         lib.vspec_execute_noalloc.restype = i
+        lib.vspec_plan_get_tuning.argtypes = [vp, ctypes.POINTER(VspecTuning), ctypes.POINTER(VspecTuning)]
+        lib.vspec_plan_get_tuning.restype = i
+        lib.vspec_plan_set_tuning.argtypes = [vp, ctypes.POINTER(VspecTuning)]
+        lib.vspec_plan_set_tuning.restype = i
         lib.vspec_status_string.argtypes = [i]
         lib.vspec_status_string.restype = cp
         lib.vspec_last_error.argtypes = []
@@ -221,6 +231,24 @@ def vspec_plan_kernel_stats(plan: int, reset: bool = False) -> list:
     return out
 
 
+def vspec_plan_get_tuning(plan: int):
+    """(current, limit) as dicts with keys chunk_spectra, blocks_a, blocks_b, assist_permille."""
+    cur, lim = VspecTuning(), VspecTuning()
+    st = load().vspec_plan_get_tuning(plan, ctypes.byref(cur), ctypes.byref(lim))
+    if st != OK:
+        raise VspecError(st, "vspec_plan_get_tuning")
+    as_dict = lambda t: {k: int(getattr(t, k)) for k, _ in VspecTuning._fields_}
+    return as_dict(cur), as_dict(lim)
+
+
+def vspec_plan_set_tuning(plan: int, chunk_spectra: int, blocks_a: int, blocks_b: int,
+                          assist_permille: int = 0) -> None:
+    t = VspecTuning(chunk_spectra, blocks_a, blocks_b, assist_permille)
+    st = load().vspec_plan_set_tuning(plan, ctypes.byref(t))
+    if st != OK:
+        raise VspecError(st, "vspec_plan_set_tuning")
+
+
 def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, window: int,
                           nspectra: int, d_accum, stream=None) -> None:
     """Allocation-free channelization (no plan, no cudaMalloc); see include/vspec.h."""
@@ -292,6 +320,12 @@ class Plan:
 
     def kernel_stats(self, reset: bool = False) -> list:
         return vspec_plan_kernel_stats(self.handle, reset)
+
+    def get_tuning(self):
+        return vspec_plan_get_tuning(self.handle)
+
+    def set_tuning(self, chunk_spectra: int, blocks_a: int, blocks_b: int, assist_permille: int = 0) -> None:
+        vspec_plan_set_tuning(self.handle, chunk_spectra, blocks_a, blocks_b, assist_permille)
 
     def close(self) -> None:
         if self.handle:

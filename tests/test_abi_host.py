@@ -60,3 +60,9 @@ def test_null_arguments_are_rejected(lib):
     assert lib.vspec_dump(None, 16, None, None) == vspec.ERR_INVALID_ARG
     assert lib.vspec_plan_info(None, None, None) == vspec.ERR_INVALID_ARG
     assert lib.vspec_plan_destroy(None) == vspec.OK
+
+
+def test_tuning_rejects_null_arguments(lib):
+    t = vspec.VspecTuning(1, 0, 1, 0)
+    assert lib.vspec_plan_get_tuning(None, None, None) == vspec.ERR_INVALID_ARG
+    assert lib.vspec_plan_set_tuning(None, ctypes.byref(t)) == vspec.ERR_INVALID_ARG

@@ -55,7 +55,7 @@ SMALL = [
     (8192, 2, 1, PFB, WIN_HANN, 7),
     (8192, 1, 2, DIRECT, WIN_HANN, 6),
     (16384, 8, 2, PFB, WIN_HANN, 10),
-    (32768, 8, 2, PFB, WIN_HANN, 67),   # two scratch chunks, ragged second chunk
+    (32768, 8, 2, PFB, WIN_HANN, 67),   # ragged: not a multiple of the clusters or tiles
     (32768, 8, 2, PFB, WIN_HANN, 1),    # fewer spectra than clusters
     (32768, 1, 2, DIRECT, WIN_HANN, 23),
     (2048, 1, 2, DIRECT, WIN_RECT, 40),
@@ -175,7 +175,12 @@ def test_error_paths_on_device():
         assert lib.vspec_execute(plan.handle, buf.data_ptr(), -1, acc.data_ptr(), s) == vspec.ERR_INVALID_ARG
         assert lib.vspec_dump(plan.handle, acc.data_ptr() + 8, None, s) == vspec.ERR_ALIGNMENT
         sb, hp = plan.info()
-        assert sb > 0 and hp == 1
+        # 1024 channels x 128 MiB of chunk scratch: the intermediate goes to HBM
+        assert sb > 0 and hp == 2
+        plan.set_tuning(64, 0, 0)  # 4 MiB chunks stay in L2
+        assert plan.info()[1] == 1
+    with vspec.Plan(32768, 8, 2, PFB, WIN_HANN) as plan:
+        assert plan.info()[1] == 1  # one-pass fused path
     with pytest.raises(vspec.VspecError) as e:
         vspec.Plan(1 << 20, 8, 2, PFB, WIN_HANN)
     assert e.value.status == vspec.ERR_UNSUPPORTED
@@ -329,3 +334,87 @@ def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
         plan.execute(d_in, s, acc)
         torch.cuda.synchronize()
         assert_close(acc.cpu().numpy().astype(np.float64).reshape(o.shape), o, what=f"{cfg} after dump")
+
+
+@pytest.mark.parametrize("cfg", [(65536, 8, 2, PFB, WIN_HANN, 37), (8192, 3, 1, PFB, WIN_HAMMING, 45),
+                                 (262144, 1, 2, DIRECT, WIN_RECT, 9)],
+                         ids=lambda c: f"N{c[0]}_P{c[1]}_pol{c[2]}_S{c[5]}")
+def test_launch_shapes_match_oracle(oracle_mod, cfg):
+    """Every launch shape of the two-kernel path (chunk length, CTAs per
+    kernel-A and kernel-B launch, including one-spectrum chunks, a single CTA,
+    CTAs that each hold a few items of several tiles, and the largest tuned
+    launch) gives the oracle's spectrum."""
+    from paper_1411_0436_gb300.vspec import Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3 if npol == 2 else 0.0,
+                tones=(Tone(25.0, n * 0.3 + 0.4, (0, 1)),))
+    x = workloads.generate(bank, 77 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
+    with Plan(n, p, npol, mode, win) as plan:
+        cur, lim = plan.get_tuning()
+        assert 1 <= cur["chunk_spectra"] <= lim["chunk_spectra"]
+        assert cur["blocks_a"] == cur["blocks_b"] == 0 and lim["blocks_a"] > 0 and lim["blocks_b"] > 0
+        shapes = [(1, 0, 0), (1, 1, 1), (min(5, lim["chunk_spectra"]), 3, 2), (2, 7, 13),
+                  (lim["chunk_spectra"], 7, lim["blocks_b"]), (lim["chunk_spectra"], 0, 1),
+                  (cur["chunk_spectra"], lim["blocks_a"], 0)]
+        for chunk, ba, bb in shapes:
+            plan.set_tuning(chunk, ba, bb)
+            acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+            plan.execute(d_in, s, acc)
+            torch.cuda.synchronize()
+            g = acc.cpu().numpy().astype(np.float64)
+            assert_close(g.reshape(n, 4) if npol == 2 else g, o, what=f"{cfg} shape {chunk, ba, bb}")
+
+
+def test_tuning_limits():
+    from paper_1411_0436_gb300.vspec import Plan, VspecError
+    import paper_1411_0436_gb300.vspec as V
+    with Plan(65536, 8, 2, PFB, WIN_HANN) as plan:
+        cur, lim = plan.get_tuning()
+        assert lim["assist_permille"] == 0
+        for bad in [(0, 0, 0), (lim["chunk_spectra"] + 1, 0, 0), (1, -1, 0), (1, lim["blocks_a"] + 1, 0),
+                    (1, 0, -1), (1, 0, lim["blocks_b"] + 1), (1, 0, 0, 5)]:
+            with pytest.raises(VspecError) as e:
+                plan.set_tuning(*bad)
+            assert e.value.status == V.ERR_INVALID_ARG
+        assert plan.get_tuning()[0] == cur  # a rejected shape changes nothing
+    with Plan(32768, 8, 2, PFB, WIN_HANN) as plan:  # one-pass fused plan
+        cur, lim = plan.get_tuning()
+        assert cur["chunk_spectra"] == cur["blocks_a"] == cur["blocks_b"] == 0
+        assert 0 <= cur["assist_permille"] <= lim["assist_permille"] <= 1000
+        for bad in [(1, 0, 0, 0), (0, 0, 1, 0), (0, 0, 0, -1), (0, 0, 0, lim["assist_permille"] + 1)]:
+            with pytest.raises(VspecError) as e:
+                plan.set_tuning(*bad)
+            assert e.value.status == V.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (32768, 1, 2, DIRECT, WIN_HAMMING, 233),
+                                 (4096, 1, 2, DIRECT, WIN_RECT, 500),
+                                 (2048, 8, 2, PFB, WIN_HAMMING, 150)],
+                         ids=lambda c: f"N{c[0]}_P{c[1]}_m{c[3]}_S{c[5]}")
+def test_fused_assist_shares_match_oracle(oracle_mod, cfg):
+    """A fused plan splits the spectra between the cluster kernel and a
+    concurrent two-kernel pass on the idle SMs; every split (none, the
+    default, half, the maximum) gives the oracle's spectrum, and the
+    profiling records cover both paths' kernels."""
+    from paper_1411_0436_gb300.vspec import Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3, tones=(Tone(25.0, n * 0.3 + 0.4, (0, 1)),))
+    x = workloads.generate(bank, 99 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
+    with Plan(n, p, npol, mode, win) as plan:
+        cur, lim = plan.get_tuning()
+        for share in sorted({0, cur["assist_permille"], min(500, lim["assist_permille"]), lim["assist_permille"]}):
+            plan.set_tuning(0, 0, 0, share)
+            plan.set_profiling(True)
+            acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+            plan.execute(d_in, s, acc)
+            torch.cuda.synchronize()
+            stats = {r[0]: r for r in plan.kernel_stats()}
+            plan.set_profiling(False)
+            assert_close(acc.cpu().numpy().astype(np.float64).reshape(n, 4), o, what=f"{cfg} assist {share}")
+            sa = stats["fir_colfft"][2]  # spectra the assist channelized
+            assert sa in (0, s * share // 1000) and (share > 0 or sa == 0)
+            assert stats["fused_channelize"][2] + sa == s
