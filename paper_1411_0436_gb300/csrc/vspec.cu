@@ -120,6 +120,7 @@ struct vspec_plan {
     int sc_cap = 1, slots_cap = 1;   // largest chunk a tuning may ask for; slots allocated
     int sc_alloc = 1;                // chunk spectra the scratch holds now
     int blocks_a = 0, blocks_b = 0;  // CTAs per kernel-A / kernel-B launch, 0: one wave
+    bool fir_b = false;              // one-row transform: kernel B only, FIR in its first pass
     size_t smemA = 0, smemB = 0;
     std::vector<Pass> passA, passB;
     float *coef = nullptr;
@@ -252,6 +253,36 @@ vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 g
         o->recs.push_back(r);
     }
     return VSPEC_OK;
+}
+
+// Fold `slots` partial-sum slots of p->partial (and p->partial_comp in
+// compensated plans) into d_accum: with more than 16 slots, first sum each
+// group of 16 slots into its first slot, then fold the group sums.
+vspec_status launch_fold(vspec_plan *p, int slots, float *d_accum, int spectra, cudaStream_t st) {
+    int groups = slots, stride = 1;
+    const int N = p->N, N1 = p->N1, N2 = p->N2;
+    if (slots > 16) {
+        groups = (slots + 15) / 16;
+        stride = 16;
+        const void *fold = p->npol == 2 ? (p->kahan ? (const void *)vspec::fold_slots_kernel<2, true>
+                                                    : (const void *)vspec::fold_slots_kernel<2, false>)
+                                        : (p->kahan ? (const void *)vspec::fold_slots_kernel<1, true>
+                                                    : (const void *)vspec::fold_slots_kernel<1, false>);
+        void *part = p->partial, *pcomp = p->partial_comp;
+        int ns = slots, n = N;
+        void *argsF[] = {&part, &pcomp, &ns, &n};
+        vspec_status r = launch(p, 2, 0, fold, dim3((N + 31) / 32, groups), dim3(32, 8), argsF, 0, st);
+        if (r != VSPEC_OK) return r;
+    }
+    const void *part = p->partial, *pcomp = p->partial_comp;
+    const int *ia = p->invA, *ib = p->invB;
+    void *outp = d_accum, *ocomp = p->out_comp;
+    if (p->kahan) {
+        void *argsR[] = {&part, &pcomp, &groups, &stride, (void *)&N, (void *)&N1, (void *)&N2, &ia, &ib, &outp, &ocomp};
+        return launch(p, 2, spectra, p->kernelR, dim3((N + 31) / 32), dim3(32, 8), argsR, 0, st);
+    }
+    void *argsR[] = {&part, &groups, &stride, (void *)&N, (void *)&N1, (void *)&N2, &ia, &ib, &outp};
+    return launch(p, 2, spectra, p->kernelR, dim3((N + 31) / 32), dim3(32, 8), argsR, 0, st);
 }
 
 const void *pick_kernel_fused(int logn1, int pt) {
@@ -473,8 +504,13 @@ vspec_status build_plan(vspec_plan *p) {
         g_last_error = "no kernel instance for this tap count and size";
         return VSPEC_ERR_UNSUPPORTED;
     }
-    p->kernelB = p->npol == 2 ? (const void *)vspec::rowfft_detect_kernel<2>
-                              : (const void *)vspec::rowfft_detect_kernel<1>;
+    // a one-row transform (N2 == 1) needs no column pass: kernel B applies the
+    // FIR to the int8 input in its first pass, and there is no chunk scratch
+    p->fir_b = N2 == 1 && !(p->flags & VSPEC_PLAN_TENSOR);
+    p->kernelB = p->npol == 2 ? (p->fir_b ? (const void *)vspec::rowfft_detect_kernel<2, false, true>
+                                          : (const void *)vspec::rowfft_detect_kernel<2>)
+                              : (p->fir_b ? (const void *)vspec::rowfft_detect_kernel<1, false, true>
+                                          : (const void *)vspec::rowfft_detect_kernel<1>);
     p->kernelR = p->npol == 2 ? (const void *)vspec::reduce_kernel<2> : (const void *)vspec::reduce_kernel<1>;
 
     const int e2 = ilog2(N2), e1 = e - e2;
@@ -508,8 +544,10 @@ vspec_status build_plan(vspec_plan *p) {
     if (p->flags & VSPEC_PLAN_KAHAN) {
         p->kahan = true;
         if (!p->tc)
-            p->kernelB = p->npol == 2 ? (const void *)vspec::rowfft_detect_kernel<2, true>
-                                      : (const void *)vspec::rowfft_detect_kernel<1, true>;
+            p->kernelB = p->npol == 2 ? (p->fir_b ? (const void *)vspec::rowfft_detect_kernel<2, true, true>
+                                                  : (const void *)vspec::rowfft_detect_kernel<2, true>)
+                                      : (p->fir_b ? (const void *)vspec::rowfft_detect_kernel<1, true, true>
+                                                  : (const void *)vspec::rowfft_detect_kernel<1, true>);
         p->kernelR = p->npol == 2 ? (const void *)vspec::reduce_kahan_kernel<2>
                                   : (const void *)vspec::reduce_kahan_kernel<1>;
     }
@@ -535,6 +573,7 @@ vspec_status build_plan(vspec_plan *p) {
     const size_t per_spec = (size_t)N * elem;
     p->sc_cap = (int)std::max<size_t>(1, kScratchCap / per_spec);
     p->sc_max = std::min({p->sc_cap, kMaxChunkSpectra, (int)std::max<size_t>(1, kScratchBudget / per_spec)});
+    if (p->fir_b) p->sc_cap = p->sc_max = kMaxChunkSpectra;  // launch length only: no scratch
     // partial-sum slots for the largest kernel-B launch a tuning may ask for
     p->slots_cap = slots_for(p, kMaxWaves * p->num_sms * p->occB);
 
@@ -548,8 +587,8 @@ vspec_status build_plan(vspec_plan *p) {
     if ((st = dev_alloc((void **)&p->twZ, sizeof(float2) * (size_t)N, &tot))) return st;
     if ((st = dev_alloc((void **)&p->invA, sizeof(int) * (size_t)N2, &tot))) return st;
     if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
-    p->sc_alloc = p->sc_max;
-    if ((st = dev_alloc(&p->Z, (size_t)p->sc_alloc * N * elem, &tot))) return st;
+    p->sc_alloc = p->fir_b ? 0 : p->sc_max;
+    if ((st = dev_alloc(&p->Z, (size_t)std::max(1, p->sc_alloc) * N * elem, &tot))) return st;
     if ((st = dev_alloc(&p->partial, (size_t)p->slots_cap * N * accel, &tot))) return st;
     if (p->tc) {
         if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
@@ -727,7 +766,7 @@ vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int 
         int l2 = 0;
         if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, plan->device) != cudaSuccess) l2 = 0;
         const size_t zb = (size_t)plan->sc_max * plan->N * (plan->npol == 2 ? sizeof(float4) : sizeof(float2));
-        *hbm_passes = (!plan->fused && zb > (size_t)l2 / 2) ? 2 : 1;
+        *hbm_passes = (!plan->fused && !plan->fir_b && zb > (size_t)l2 / 2) ? 2 : 1;
     }
     return VSPEC_OK;
 }
@@ -763,7 +802,7 @@ vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
         g_last_error = "tuning value out of range";
         return VSPEC_ERR_INVALID_ARG;
     }
-    if (t->chunk_spectra > plan->sc_alloc) {  // grow the chunk scratch
+    if (!plan->fir_b && t->chunk_spectra > plan->sc_alloc) {  // grow the chunk scratch
         const size_t elem = plan->npol == 2 ? sizeof(float4) : sizeof(float2);
         const size_t old_bytes = (size_t)plan->sc_alloc * plan->N * elem;
         void *z = nullptr;
@@ -841,12 +880,7 @@ static vspec_status run_fused(vspec_plan *p, const int8_t *d_in, int nspectra, f
         vspec_status r = launch(p, 3, nspectra, p->kernelF, dim3(p->cluster * p->nclusters),
                                 dim3(vspec::fusedw::kThreads), argsW, p->smemF, st, p->cluster);
         if (r != VSPEC_OK) return r;
-        const void *part = p->partial;
-        int groups = p->nclusters, N = p->N, N1 = p->N1, N2 = p->N2;
-        const int *ia = p->invA, *ib = p->invB;
-        void *outp = d_accum;
-        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
-        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+        return launch_fold(p, p->nclusters, d_accum, nspectra, st);
     }
     if (p->fused) {
         vspec::fused::Params fp;
@@ -865,12 +899,7 @@ static vspec_status run_fused(vspec_plan *p, const int8_t *d_in, int nspectra, f
         vspec_status r = launch(p, 3, nspectra, p->kernelF, dim3(p->cluster * p->nclusters),
                                 dim3(vspec::fused::kThreads), argsF, p->smemF, st, p->cluster);
         if (r != VSPEC_OK) return r;
-        const void *part = p->partial;
-        int groups = p->nclusters, N = p->N, N1 = p->N1, N2 = p->N2;
-        const int *ia = p->invA, *ib = p->invB;
-        void *outp = d_accum;
-        void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
-        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+        return launch_fold(p, p->nclusters, d_accum, nspectra, st);
     }
     return VSPEC_OK;
 }
@@ -885,15 +914,16 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     // over them (block_span), so every SM stays busy to the end of a launch
     const int nA = p->blocks_a > 0 ? p->blocks_a : p->num_sms * p->occA;
     const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
-    const int slots = slots_for(p, nB);
-    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
-    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
-
     // equal chunks of at most sc_max spectra (no short ragged last chunk)
     const int nchunks = (nspectra + p->sc_max - 1) / p->sc_max;
     const int sc_full = (nspectra + nchunks - 1) / nchunks;
+    // slots of the largest kernel-B launch (no more CTAs than items)
+    const int tilesB = p->N2 / p->RB;
+    const int slots = slots_for(p, (int)std::min<long long>(nB, (long long)tilesB * sc_full));
+    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
+    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
 
-    vspec::ColParams ca;
+    vspec::ColParams ca{};
     ca.in = d_in;
     ca.coef = p->coef;
     ca.twA = p->twA;
@@ -910,7 +940,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
     ca.tiles = p->N1 / p->C;
 
-    vspec::RowParams cb;
+    vspec::RowParams cb{};
     cb.Z = p->Z;
     cb.partial = p->partial;
     cb.partial_comp = p->partial_comp;
@@ -925,16 +955,23 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     for (int i = 0; i < cb.npass; i++) cb.pass[i] = p->passB[i];
     cb.tiles = p->N2 / p->RB;
     cb.slots = slots;
+    cb.in = d_in;
+    cb.coef = p->coef;
+    cb.P = p->P;
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);
-        ca.s0 = s0;
-        ca.sc = sc;
-        void *argsA[] = {&ca};
-        // no more CTAs than items: every block then has work
-        const int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
-        vspec_status r = launch(p, 0, sc, p->kernelA, dim3(ga), dim3(p->TA), argsA, p->smemA, st);
-        if (r != VSPEC_OK) return r;
+        if (!p->fir_b) {
+            ca.s0 = s0;
+            ca.sc = sc;
+            void *argsA[] = {&ca};
+            // no more CTAs than items: every block then has work
+            const int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
+            vspec_status r = launch(p, 0, sc, p->kernelA, dim3(ga), dim3(p->TA), argsA, p->smemA, st);
+            if (r != VSPEC_OK) return r;
+        }
+        vspec_status r;
+        cb.s0 = s0;
         cb.sc = sc;
         vspec::TcStatus ts{p->tc_status};
         void *argsB[] = {&cb, &ts};
@@ -943,20 +980,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
         if (r != VSPEC_OK) return r;
     }
     if (before_fold) VSPEC_CUDA(cudaStreamWaitEvent(st, before_fold, 0));
-    if (p->kahan) {
-        const void *part = p->partial, *pcomp = p->partial_comp;
-        int groups = slots, N = p->N, N1 = p->N1, N2 = p->N2;
-        const int *ia = p->invA, *ib = p->invB;
-        void *outp = d_accum, *ocomp = p->out_comp;
-        void *argsR[] = {&part, &pcomp, &groups, &N, &N1, &N2, &ia, &ib, &outp, &ocomp};
-        return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
-    }
-    const void *part = p->partial;
-    int groups = slots, N = p->N, N1 = p->N1, N2 = p->N2;
-    const int *ia = p->invA, *ib = p->invB;
-    void *outp = d_accum;
-    void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
-    return launch(p, 2, nspectra, p->kernelR, dim3((p->N + 255) / 256), dim3(256), argsR, 0, st);
+    return launch_fold(p, slots, d_accum, nspectra, st);
 }
 
 static vspec_status execute_one(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
@@ -1346,7 +1370,7 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     const size_t accel = npol == 2 ? sizeof(float4) : sizeof(float);
     VSPEC_CUDA(cudaMemsetAsync(partial, 0, (size_t)c.slots * c.N * accel, st));
 
-    vspec::ColParams ca;
+    vspec::ColParams ca{};
     ca.in = d_in;
     ca.coef = coef;
     ca.twA = twA;
@@ -1361,7 +1385,7 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     ca.lN2 = ilog2(c.N2);
     ca.npass = c.nA;
     for (int i = 0; i < c.nA; i++) ca.pass[i] = c.passA[i];
-    vspec::RowParams cb;
+    vspec::RowParams cb{};
     cb.Z = Z;
     cb.partial = partial;
     cb.twB = twB;
@@ -1391,10 +1415,10 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
         VSPEC_CUDA(cudaLaunchKernel(c.kB, dim3(gb), dim3(c.TB), argsB, c.smemB, st));
     }
     const void *part = partial;
-    int groups = c.slots, N = c.N, N1 = c.N1, N2 = c.N2;
+    int groups = c.slots, stride = 1, N = c.N, N1 = c.N1, N2 = c.N2;  // at most 16 slots
     const int *ia = invA, *ib = invB;
     void *outp = d_accum;
-    void *argsR[] = {&part, &groups, &N, &N1, &N2, &ia, &ib, &outp};
-    VSPEC_CUDA(cudaLaunchKernel(c.kR, dim3((c.N + 255) / 256), dim3(256), argsR, 0, st));
+    void *argsR[] = {&part, &groups, &stride, &N, &N1, &N2, &ia, &ib, &outp};
+    VSPEC_CUDA(cudaLaunchKernel(c.kR, dim3((c.N + 31) / 32), dim3(32, 8), argsR, 0, st));
     return VSPEC_OK;
 }

@@ -64,6 +64,12 @@ struct RowParams {
     int sc;              // spectra in this chunk
     int tiles;           // row tiles, N2 / RB
     int slots;           // partial-sum slots (span_slot bound)
+    // N2 == 1 (the row is the whole transform): the first pass reads the
+    // int8 input and applies the FIR itself instead of reading Z
+    const int8_t *in;
+    const float *coef;
+    int P;
+    long long s0;        // absolute index of the chunk's first spectrum
 };
 
 // ------------------------------------------------------------ work split --
@@ -324,17 +330,39 @@ __device__ __forceinline__ float4 sub4(float4 a, float4 b) {
     return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
-template <int R, int NPOL, bool KAHAN = false>
+// Pre-filter output y_s[n] = sum_t h[t N + n] x[(s + t) N + n] of one sample
+// (h[0] on the oldest frame), straight from the int8 input.
+template <int NPOL>
+__device__ __forceinline__ typename Elem<NPOL>::T fir_sample(const RowParams &p, long long sabs, int n) {
+    constexpr int NC = 2 * NPOL;
+    float a[NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) a[k] = 0.f;
+    for (int t = 0; t < p.P; t++) {
+        const float c = __ldg(p.coef + (size_t)t * p.N + n);
+        const uint32_t w = load_raw<NPOL>(p.in, (sabs + t) * p.N + n) ^ 0x80808080u;
+#pragma unroll
+        for (int k = 0; k < NC; k++) a[k] = fmaf(c, unpack_byte(w, k), a[k]);
+    }
+    if constexpr (NPOL == 2) return make_float4(a[0], a[1], a[2], a[3]);
+    else return make_float2(a[0], a[1]);
+}
+
+template <int R, int NPOL, bool KAHAN = false, bool FIR = false>
 __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::Acc *acc,
                                               const typename Elem<NPOL>::T *Zs, const Pass ps,
                                               bool first, bool last, int r, int b, int j,
-                                              int rowstride, typename Elem<NPOL>::Acc *comp = nullptr) {
+                                              int rowstride, typename Elem<NPOL>::Acc *comp = nullptr,
+                                              long long sabs = 0) {
     using T = typename Elem<NPOL>::T;
     const int base = b * ps.lb + j;
     T *row = data + r * rowstride;
     T v[R];
-    if (first) {
+    if (FIR && first) {
+#pragma unroll
+        for (int q = 0; q < R; q++) v[q] = fir_sample<NPOL>(p, sabs, base + q * ps.m);
+    } else if (first) {
         const T *zr = Zs + (size_t)(x * p.RB + r) * p.N1;
 #pragma unroll
         for (int q = 0; q < R; q++) v[q] = zr[base + q * ps.m];
@@ -369,7 +397,7 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typenam
     }
 }
 
-template <int NPOL, bool KAHAN = false>
+template <int NPOL, bool KAHAN = false, bool FIR = false>
 __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_constant__ RowParams p) {
     using T = typename Elem<NPOL>::T;
     using A = typename Elem<NPOL>::Acc;
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
         __syncthreads();
 
         for (int s = s_beg; s < s_end; s++) {
-            const T *Zs = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
+            const T *Zs = FIR ? nullptr : reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
             for (int ip = 0; ip < p.npass; ip++) {
                 const Pass ps = p.pass[ip];
                 const bool first = ip == 0, last = ip == p.npass - 1;
@@ -408,11 +436,12 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
                 for (int u = threadIdx.x; u < nb; u += blockDim.x) {
                     const int r = u >> lper, w = u & ((1 << lper) - 1);
                     const int b = w >> ps.lm, j = w & (ps.m - 1);
+                    const long long sabs = p.s0 + s;
                     switch (ps.r) {
-                        case 2: row_butterfly<2, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                        case 4: row_butterfly<4, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                        case 8: row_butterfly<8, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
-                        default: row_butterfly<16, NPOL, KAHAN>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp); break;
+                        case 2: row_butterfly<2, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
+                        case 4: row_butterfly<4, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
+                        case 8: row_butterfly<8, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
+                        default: row_butterfly<16, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
                     }
                 }
                 __syncthreads();
@@ -472,68 +501,173 @@ __global__ void deinterleave_kernel(const W *in, W *out, int nsub, long long M, 
 }
 
 // ------------------------------------------------------------------ reduce --
-// d_accum[k] += sum over groups of partial[g][posA(k2) * N1 + posB(k1)].
-template <int NPOL>
-__global__ void reduce_kernel(const void *partial, int groups, int N, int N1, int N2,
-                              const int *invA, const int *invB, void *out) {
+// First level of the fold when there are many slots (small transforms split
+// over many CTAs): slot group g (slots 16g .. 16g+15) is summed, in slot
+// order, into slot 16g; the compensated variant sums the compensated values
+// with Kahan additions and leaves a zero compensation. blockDim (32, 8):
+// 32 positions x 8 slot lanes; gridDim (ceil(N / 32), groups of 16).
+template <int NPOL, bool KAHAN>
+__global__ void __launch_bounds__(256) fold_slots_kernel(void *partial, void *partial_comp, int slots, int N) {
     using A = typename Elem<NPOL>::Acc;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const int k2 = k & (N2 - 1), k1 = k / N2;
-    const size_t idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
-    const A *pp = reinterpret_cast<const A *>(partial);
-    A *o = reinterpret_cast<A *>(out);
-    if constexpr (NPOL == 2) {
-        float4 s = pp[idx];
-        for (int g = 1; g < groups; g++) {
-            const float4 v = pp[(size_t)g * N + idx];
-            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    __shared__ A lane_sum[8][32];
+    __shared__ A lane_comp[8][32];
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int y = threadIdx.y;
+    const int g0 = blockIdx.y * 16;
+    A *pp = reinterpret_cast<A *>(partial);
+    A *pc = reinterpret_cast<A *>(partial_comp);
+    A s, c;
+    if constexpr (NPOL == 2) s = make_float4(0.f, 0.f, 0.f, 0.f);
+    else s = 0.f;
+    c = s;
+    if (i < N) {
+        for (int g = g0 + y; g < min(slots, g0 + 16); g += 8) {
+            const size_t o = (size_t)g * N + i;
+            if constexpr (KAHAN) {
+                if constexpr (NPOL == 2) kahan_add(s, c, sub4(pp[o], pc[o]));
+                else kahan_add(s, c, pp[o] - pc[o]);
+            } else if constexpr (NPOL == 2) {
+                const float4 v = pp[o];
+                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            } else {
+                s += pp[o];
+            }
         }
-        float4 a = o[k];
+    }
+    lane_sum[y][threadIdx.x] = s;
+    lane_comp[y][threadIdx.x] = c;
+    __syncthreads();  // every lane has read its slots before slot g0 is written
+    if (y != 0 || i >= N) return;
+    if constexpr (KAHAN) {
+        A t, tc;
+        if constexpr (NPOL == 2) {
+            t = sub4(s, c);
+            tc = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            t = s - c;
+            tc = 0.f;
+        }
+#pragma unroll
+        for (int l = 1; l < 8; l++) {
+            if constexpr (NPOL == 2) kahan_add(t, tc, sub4(lane_sum[l][threadIdx.x], lane_comp[l][threadIdx.x]));
+            else kahan_add(t, tc, lane_sum[l][threadIdx.x] - lane_comp[l][threadIdx.x]);
+        }
+        if constexpr (NPOL == 2) {
+            pp[(size_t)g0 * N + i] = sub4(t, tc);
+            pc[(size_t)g0 * N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            pp[(size_t)g0 * N + i] = t - tc;
+            pc[(size_t)g0 * N + i] = 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int l = 1; l < 8; l++) {
+            const A v = lane_sum[l][threadIdx.x];
+            if constexpr (NPOL == 2) {
+                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            } else {
+                s += v;
+            }
+        }
+        pp[(size_t)g0 * N + i] = s;
+    }
+}
+
+// Fold of the partial-sum slots into the caller's accumulator, with the
+// digit-reversal scatter of the four-step FFT: channel k = k1 * N2 + k2 sits
+// at position invA[k2] * N1 + invB[k1] of every slot (slot g at g * stride).
+// A block is 32 channels x 8 slot lanes (blockDim (32, 8)): lane y sums
+// slots y, y + 8, ..., and lane 0 adds the eight lane sums in order.
+template <int NPOL>
+__global__ void __launch_bounds__(256) reduce_kernel(const void *partial, int groups, int stride, int N, int N1,
+                                                     int N2, const int *invA, const int *invB, void *out) {
+    using A = typename Elem<NPOL>::Acc;
+    __shared__ A lane_sum[8][32];
+    const int k = blockIdx.x * 32 + threadIdx.x;
+    const int y = threadIdx.y;
+    const A *pp = reinterpret_cast<const A *>(partial);
+    A s;
+    if constexpr (NPOL == 2) s = make_float4(0.f, 0.f, 0.f, 0.f);
+    else s = 0.f;
+    size_t idx = 0;
+    if (k < N) {
+        const int k2 = k & (N2 - 1), k1 = k / N2;
+        idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
+        for (int g = y; g < groups; g += 8) {
+            const A v = pp[(size_t)g * stride * N + idx];
+            if constexpr (NPOL == 2) {
+                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            } else {
+                s += v;
+            }
+        }
+    }
+    lane_sum[y][threadIdx.x] = s;
+    __syncthreads();
+    if (y != 0 || k >= N) return;
+    A *o = reinterpret_cast<A *>(out);
+#pragma unroll
+    for (int l = 1; l < 8; l++) {
+        const A v = lane_sum[l][threadIdx.x];
+        if constexpr (NPOL == 2) {
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        } else {
+            s += v;
+        }
+    }
+    if constexpr (NPOL == 2) {
+        const float4 a = o[k];
         o[k] = make_float4(a.x + s.x, a.y + s.y, a.z + s.z, a.w + s.w);
     } else {
-        float s = pp[idx];
-        for (int g = 1; g < groups; g++) s += pp[(size_t)g * N + idx];
         o[k] += s;
     }
 }
 
-// Compensated reduce: Kahan sum of the compensated group partials, then a
-// compensated add into the caller's accumulator with the plan-owned
-// compensation out_comp (cleared by vspec_dump).
+// Compensated fold: each lane keeps a Kahan sum of its slots' compensated
+// partials; lane 0 folds the eight lanes' compensated totals with Kahan
+// additions and then adds the result into the caller's accumulator with the
+// plan-owned compensation out_comp (cleared by vspec_dump).
 template <int NPOL>
-__global__ void reduce_kahan_kernel(const void *partial, const void *partial_comp, int groups, int N, int N1,
-                                    int N2, const int *invA, const int *invB, void *out, void *out_comp) {
+__global__ void __launch_bounds__(256) reduce_kahan_kernel(const void *partial, const void *partial_comp,
+                                                           int groups, int stride, int N, int N1, int N2,
+                                                           const int *invA, const int *invB, void *out,
+                                                           void *out_comp) {
     using A = typename Elem<NPOL>::Acc;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const int k2 = k & (N2 - 1), k1 = k / N2;
-    const size_t idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
+    __shared__ A lane_sum[8][32];
+    const int k = blockIdx.x * 32 + threadIdx.x;
+    const int y = threadIdx.y;
     const A *pp = reinterpret_cast<const A *>(partial);
     const A *pc = reinterpret_cast<const A *>(partial_comp);
+    A s, c;
+    if constexpr (NPOL == 2) s = make_float4(0.f, 0.f, 0.f, 0.f);
+    else s = 0.f;
+    c = s;
+    if (k < N) {
+        const int k2 = k & (N2 - 1), k1 = k / N2;
+        const size_t idx = (size_t)__ldg(invA + k2) * N1 + __ldg(invB + k1);
+        for (int g = y; g < groups; g += 8) {
+            const size_t o = (size_t)g * stride * N + idx;
+            if constexpr (NPOL == 2) kahan_add(s, c, sub4(pp[o], pc[o]));
+            else kahan_add(s, c, pp[o] - pc[o]);
+        }
+    }
+    if constexpr (NPOL == 2) lane_sum[y][threadIdx.x] = sub4(s, c);
+    else lane_sum[y][threadIdx.x] = s - c;
+    __syncthreads();
+    if (y != 0 || k >= N) return;
+    A t = lane_sum[0][threadIdx.x], tc;
+    if constexpr (NPOL == 2) tc = make_float4(0.f, 0.f, 0.f, 0.f);
+    else tc = 0.f;
+#pragma unroll
+    for (int l = 1; l < 8; l++) kahan_add(t, tc, lane_sum[l][threadIdx.x]);
     A *o = reinterpret_cast<A *>(out);
     A *oc = reinterpret_cast<A *>(out_comp);
-    A s, c;
-    if constexpr (NPOL == 2) {
-        s = make_float4(0.f, 0.f, 0.f, 0.f);
-        c = s;
-        for (int g = 0; g < groups; g++)
-            kahan_add(s, c, sub4(pp[(size_t)g * N + idx], pc[(size_t)g * N + idx]));
-        float4 a = o[k], ac = oc[k];
-        kahan_add(a, ac, sub4(s, c));
-        kahan_settle(a, ac);
-        o[k] = a;
-        oc[k] = ac;
-    } else {
-        s = 0.f;
-        c = 0.f;
-        for (int g = 0; g < groups; g++) kahan_add(s, c, pp[(size_t)g * N + idx] - pc[(size_t)g * N + idx]);
-        float a = o[k], ac = oc[k];
-        kahan_add(a, ac, s - c);
-        kahan_settle(a, ac);
-        o[k] = a;
-        oc[k] = ac;
-    }
+    A a = o[k], ac = oc[k];
+    if constexpr (NPOL == 2) kahan_add(a, ac, sub4(t, tc));
+    else kahan_add(a, ac, t - tc);
+    kahan_settle(a, ac);
+    o[k] = a;
+    oc[k] = ac;
 }
 
 // ------------------------------------------------------ plan-time tables ---

@@ -175,9 +175,10 @@ def test_error_paths_on_device():
         assert lib.vspec_execute(plan.handle, buf.data_ptr(), -1, acc.data_ptr(), s) == vspec.ERR_INVALID_ARG
         assert lib.vspec_dump(plan.handle, acc.data_ptr() + 8, None, s) == vspec.ERR_ALIGNMENT
         sb, hp = plan.info()
-        # 1024 channels x 128 MiB of chunk scratch: the intermediate goes to HBM
-        assert sb > 0 and hp == 2
-        plan.set_tuning(64, 0, 0)  # 4 MiB chunks stay in L2
+        assert sb > 0 and hp == 1  # one-row transform: FIR, FFT and detection in one kernel
+    with vspec.Plan(131072, 8, 2, PFB, WIN_HANN) as plan:
+        assert plan.info()[1] == 2  # 512 MiB chunk scratch: the intermediate goes through HBM
+        plan.set_tuning(16, 0, 0)   # 32 MiB chunks stay in L2
         assert plan.info()[1] == 1
     with vspec.Plan(32768, 8, 2, PFB, WIN_HANN) as plan:
         assert plan.info()[1] == 1  # one-pass fused path
@@ -309,7 +310,8 @@ def test_tensor_core_plan_rejects_other_sizes():
 
 
 @pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 67), (4096, 1, 1, DIRECT, WIN_RECT, 40),
-                                 (131072, 8, 2, PFB, WIN_HANN, 5)])
+                                 (131072, 8, 2, PFB, WIN_HANN, 5), (1024, 8, 2, PFB, WIN_HANN, 500),
+                                 (512, 1, 1, DIRECT, WIN_RECT, 700)])
 def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
     """Kahan accumulation (alone and with the tensor-core pass) stays within
     the tolerances; dump clears the compensation with the accumulator."""
@@ -323,7 +325,7 @@ def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
     mk = assert_close(run_gpu(bank, x, flags=PLAN_KAHAN), o, what=f"{cfg} kahan")
     mp = metrics(run_gpu(bank, x, flags=1), o)
     print(f"\n{cfg}: normalised max error plain {mp['pure']:.3e}, compensated {mk['pure']:.3e}")
-    if npol == 2:
+    if npol == 2 and 2048 <= n <= 524288:  # the tensor-core pass needs 2048-point rows
         assert_close(run_gpu(bank, x, flags=PLAN_KAHAN | PLAN_TENSOR), o, atol=ATOL_TC, rtol=RTOL_TC,
                      what=f"{cfg} kahan+tensor")
     with Plan(n, p, npol, mode, win, PLAN_KAHAN) as plan:  # twice, dump in between
@@ -337,7 +339,8 @@ def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
 
 
 @pytest.mark.parametrize("cfg", [(65536, 8, 2, PFB, WIN_HANN, 37), (8192, 3, 1, PFB, WIN_HAMMING, 45),
-                                 (262144, 1, 2, DIRECT, WIN_RECT, 9)],
+                                 (262144, 1, 2, DIRECT, WIN_RECT, 9), (1024, 8, 2, PFB, WIN_HANN, 300),
+                                 (2048, 5, 1, PFB, WIN_HAMMING, 61)],
                          ids=lambda c: f"N{c[0]}_P{c[1]}_pol{c[2]}_S{c[5]}")
 def test_launch_shapes_match_oracle(oracle_mod, cfg):
     """Every launch shape of the two-kernel path (chunk length, CTAs per
