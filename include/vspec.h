@@ -75,8 +75,9 @@ typedef struct vspec_plan vspec_plan;
  * bound to the device that is current at creation. On success *out holds the
  * plan; on failure *out is set to NULL and nothing is leaked.
  * Errors: VSPEC_ERR_INVALID_ARG (bad argument or out == NULL),
- * VSPEC_ERR_UNSUPPORTED (a PFB with nchan above the sizes this build's
- * kernels hold on chip), VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
+ * VSPEC_ERR_OOM, VSPEC_ERR_CUDA. Every valid (nchan, ntaps, npol, mode,
+ * window) is implemented; VSPEC_ERR_UNSUPPORTED comes only from the flags of
+ * vspec_plan_create_ex and the sub-band limits of vspec_plan_create_sb.
  */
 VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
                                vspec_mode mode, vspec_window window);

@@ -121,6 +121,7 @@ struct vspec_plan {
     int sc_alloc = 1;                // chunk spectra the scratch holds now
     int blocks_a = 0, blocks_b = 0;  // CTAs per kernel-A / kernel-B launch, 0: one wave
     bool fir_b = false;              // one-row transform: kernel B only, FIR in its first pass
+    bool gather = false;             // long PFB: kernel A reads the FIR taps from the input
     size_t smemA = 0, smemB = 0;
     std::vector<Pass> passA, passB;
     float *coef = nullptr;
@@ -171,6 +172,17 @@ struct vspec_plan {
 };
 
 namespace {
+
+template <int NPOL> const void *pick_kernel_gather(int PPT) {
+    using namespace vspec;
+    switch (PPT) {
+        case 1: return (const void *)fir_colfft_gather_kernel<NPOL, 1>;
+        case 2: return (const void *)fir_colfft_gather_kernel<NPOL, 2>;
+        case 4: return (const void *)fir_colfft_gather_kernel<NPOL, 4>;
+        case 8: return (const void *)fir_colfft_gather_kernel<NPOL, 8>;
+        default: return nullptr;
+    }
+}
 
 template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
     using namespace vspec;
@@ -469,16 +481,29 @@ vspec_status build_plan(vspec_plan *p) {
     if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN)) && p->npol == 2 && N >= 2048 &&
         N <= 32768 && (!pfb || p->P == 8))
         return build_fused_plan(p);
-    const int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
-    const int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
-    // largest column length kernel A can hold in registers (512 threads)
-    int n2max;
-    if (!pfb) n2max = 4096 / cmin;
-    else if (PT <= 8) n2max = 1024 / cmin;
-    else n2max = 512 / cmin;
+    int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
+    int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
+    // largest column length kernel A can hold in registers (512 threads, at
+    // most 4096 points, the FIR window's registers allowing)
+    auto n2max = [&]() { return PT == 1 ? 4096 / cmin : PT <= 8 ? 1024 / cmin : 512 / cmin; };
     // smallest N2 that brings N1 to at most 2048 (4096 if the columns are full)
     int N2 = 1;
-    while (N / N2 > kRowElems && N2 < n2max) N2 *= 2;
+    auto grow = [&]() {
+        while (N / N2 > kRowElems && N2 < n2max()) N2 *= 2;
+    };
+    grow();
+    // a PFB too long for the register FIR window reads its taps from the
+    // input instead (kernel A's gather form), with direct-mode column tiles
+    p->gather = pfb && N / N2 > 4096;
+    if (p->gather) {
+        PT = 1;
+        grow();
+    }
+    // single-pol at the largest sizes: 32-byte row segments, longer columns
+    if (N / N2 > 4096 && cmin == 32) {
+        cmin = 16;
+        grow();
+    }
     const int N1 = N / N2;
     if (N1 > 4096) {
         g_last_error = "nchan too large for this mode in this build";
@@ -499,7 +524,8 @@ vspec_status build_plan(vspec_plan *p) {
     p->PT = PT;
     p->PPT = PPT;
     p->TA = TA;
-    p->kernelA = p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT);
+    p->kernelA = p->gather ? (p->npol == 2 ? pick_kernel_gather<2>(PPT) : pick_kernel_gather<1>(PPT))
+                           : (p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT));
     if (!p->kernelA) {
         g_last_error = "no kernel instance for this tap count and size";
         return VSPEC_ERR_UNSUPPORTED;

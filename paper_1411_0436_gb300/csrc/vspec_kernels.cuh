@@ -279,6 +279,59 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     }
 }
 
+// Kernel A for transforms too long for a register FIR window next to the
+// column tile (PFB with nchan above 2^18): every spectrum's P taps are read
+// straight from the input (the P frames a spectrum spans stay in L2 while
+// the block walks its consecutive spectra), the coefficients from L1/L2.
+template <int NPOL, int PPT>
+__global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_constant__ ColParams p) {
+    using T = typename Elem<NPOL>::T;
+    constexpr int NC = 2 * NPOL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *data = reinterpret_cast<T *>(smem_raw);  // [N2][C]
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        long long n_pt[PPT];
+#pragma unroll
+        for (int i = 0; i < PPT; i++) {
+            const int idx = threadIdx.x + i * blockDim.x;  // = n2 * C + c
+            n_pt[i] = x * p.C + (idx & (p.C - 1)) + (long long)p.N1 * (idx >> p.lC);
+        }
+        for (int s = s_beg; s < s_end; s++) {
+            const long long f0 = p.s0 + s;  // oldest frame of spectrum s
+            float y[PPT][NC];
+#pragma unroll
+            for (int i = 0; i < PPT; i++)
+#pragma unroll
+                for (int k = 0; k < NC; k++) y[i][k] = 0.f;
+#pragma unroll 4
+            for (int t = 0; t < p.P; t++) {
+#pragma unroll
+                for (int i = 0; i < PPT; i++) {
+                    const float c = __ldg(p.coef + (size_t)t * p.N + n_pt[i]);
+                    const uint32_t wx = load_raw<NPOL>(p.in, (f0 + t) * p.N + n_pt[i]) ^ 0x80808080u;
+#pragma unroll
+                    for (int k = 0; k < NC; k++) y[i][k] = fmaf(c, unpack_byte(wx, k), y[i][k]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < PPT; i++) {
+                T *d = data + threadIdx.x + i * blockDim.x;
+                if constexpr (NPOL == 2) *d = make_float4(y[i][0], y[i][1], y[i][2], y[i][3]);
+                else *d = make_float2(y[i][0], y[i][1]);
+            }
+            __syncthreads();
+            // ends on a barrier: data is free for the next spectrum
+            col_fft_store<NPOL, col_radix_cap(NPOL, 1, PPT)>(p, data, x, s, 1);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- kernel B --
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }

@@ -67,6 +67,11 @@ SMALL = [
     (262144, 8, 2, PFB, WIN_HANN, 2),
     (524288, 1, 2, DIRECT, WIN_RECT, 2),
     (1 << 20, 1, 2, DIRECT, WIN_RECT, 1),
+    (1 << 19, 8, 2, PFB, WIN_HANN, 3),     # taps read from the input (no register window)
+    (1 << 20, 8, 2, PFB, WIN_HAMMING, 2),
+    (1 << 20, 16, 1, PFB, WIN_HANN, 2),
+    (1 << 20, 1, 1, DIRECT, WIN_RECT, 2),  # single-pol, 32-byte column segments
+    (1 << 18, 16, 2, PFB, WIN_HANN, 3),
 ]
 
 
@@ -182,9 +187,6 @@ def test_error_paths_on_device():
         assert plan.info()[1] == 1
     with vspec.Plan(32768, 8, 2, PFB, WIN_HANN) as plan:
         assert plan.info()[1] == 1  # one-pass fused path
-    with pytest.raises(vspec.VspecError) as e:
-        vspec.Plan(1 << 20, 8, 2, PFB, WIN_HANN)
-    assert e.value.status == vspec.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (1024, 8, 1, PFB, WIN_HANN, 70),
