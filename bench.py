@@ -284,6 +284,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     config = args.config
     bank = workloads.CONFIGS[config][0]
+    if args.spectra:  # a shorter dump of the same workload (profiling captures)
+        import dataclasses
+        bank = dataclasses.replace(bank, nspectra=min(args.spectra, bank.nspectra))
     # each rank is an independent beam: its own seeded input
     x = workloads.generate(bank, beam_seed(rank, config))
     in_bytes = x.nbytes
@@ -635,6 +638,8 @@ def main():
                     help="skip the tensor-core and two-kernel comparison runs")
     ap.add_argument("--sweep", action="store_true",
                     help="bandwidth against FFT length and accumulation length (Fig. 3 shape)")
+    ap.add_argument("--spectra", type=int, default=0,
+                    help="channelize only the first SPECTRA spectra of the dump (smaller profiling captures)")
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
                     help="c2: the 32768-channel PFB dump (default); c1, c3, c4: the other single-bank "
                          "workloads; c5: the batched multi-beam workload")

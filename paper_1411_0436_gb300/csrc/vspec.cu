@@ -580,10 +580,25 @@ vspec_status build_plan(vspec_plan *p) {
 
     const size_t elem = p->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
-    p->smemA = (size_t)PT * N2 * C * elem;
+    p->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2);  // + twiddle tile
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
     if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);
+    // 2048-point rows (radix 16, 16, 8): the paired-spectra row kernel with
+    // register accumulators
+    if (!p->tc && N1 == 2048 && p->RB == 1 && p->passB.size() == 3 && p->passB[0].r == 16 &&
+        p->passB[1].r == 16 && p->passB[2].r == 8) {
+        using namespace vspec;
+        const bool k = p->kahan, f = p->fir_b;
+        if (p->npol == 2)
+            p->kernelB = k ? (f ? (const void *)row2048_kernel<2, true, true> : (const void *)row2048_kernel<2, true, false>)
+                           : (f ? (const void *)row2048_kernel<2, false, true> : (const void *)row2048_kernel<2, false, false>);
+        else
+            p->kernelB = k ? (f ? (const void *)row2048_kernel<1, true, true> : (const void *)row2048_kernel<1, true, false>)
+                           : (f ? (const void *)row2048_kernel<1, false, true> : (const void *)row2048_kernel<1, false, false>);
+        p->TB = 256;
+        p->smemB = 2 * (size_t)kRow2048Stride * elem;
+    }
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -1301,7 +1316,7 @@ vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
     c->TB = std::min(256, std::max(32, maxb));
     const size_t elem = c->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = c->npol == 2 ? sizeof(float4) : sizeof(float);
-    c->smemA = (size_t)PT * N2 * C * elem;
+    c->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2);  // + twiddle tile
     c->smemB = (size_t)c->RB * (N1 + (N1 >> 4)) * elem + (size_t)c->RB * N1 * accel;
     VSPEC_CUDA(raise_smem_cap(c->kA, c->smemA));
     VSPEC_CUDA(raise_smem_cap(c->kB, c->smemB));

@@ -114,7 +114,7 @@ template <> __device__ __forceinline__ uint32_t load_raw<1>(const int8_t *in, lo
 template <int R, int NPOL>
 __device__ __forceinline__ void col_butterfly(const ColParams &p, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::T *Zs, const Pass ps,
-                                              bool last, int c, int b, int j, int n1) {
+                                              bool last, int c, int b, int j, int n1, const float2 *tws) {
     using T = typename Elem<NPOL>::T;
     const int C = p.C;
     const int base = b * ps.lb + j;
@@ -135,16 +135,17 @@ __device__ __forceinline__ void col_butterfly(const ColParams &p, typename Elem<
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const size_t zi = (size_t)(base + q) * p.N1 + n1;
-            Zs[zi] = cmul(v[q], __ldg(p.twZ + zi));
+            Zs[zi] = cmul(v[q], tws[(base + q) * C + c]);
         }
     }
 }
 
 // Column DFTs of a batch of nb spectra (data holds their pre-filter outputs,
 // [spectrum][n2][c]), then W_N^(n1 k2) and the store into the chunk scratch.
+// tws: the tile's four-step twiddles W_N^(n1 k2(pos)), [pos][c], in shared memory.
 template <int NPOL, int RMAX>
 __device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<NPOL>::T *data,
-                                              int x, int s_local0, int nb) {
+                                              int x, int s_local0, int nb, const float2 *tws) {
     using T = typename Elem<NPOL>::T;
     const int C = p.C, N2 = p.N2;
     const int pts = N2 * C;
@@ -166,14 +167,25 @@ __device__ __forceinline__ void col_fft_store(const ColParams &p, typename Elem<
             const int b = bj >> ps.lm, j = bj & (ps.m - 1);
             T *d = data + sb * pts;
             T *Zs = reinterpret_cast<T *>(p.Z) + (size_t)(s_local0 + sb) * p.N;
-            if (ps.r == 2) col_butterfly<2, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
-            else if (ps.r == 4 || RMAX < 8) col_butterfly<4, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
-            else if (ps.r == 8 || RMAX < 16) col_butterfly<(RMAX < 8 ? 4 : 8), NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
-            else col_butterfly<RMAX, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c);
+            if (ps.r == 2) col_butterfly<2, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c, tws);
+            else if (ps.r == 4 || RMAX < 8) col_butterfly<4, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c, tws);
+            else if (ps.r == 8 || RMAX < 16) col_butterfly<(RMAX < 8 ? 4 : 8), NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c, tws);
+            else col_butterfly<RMAX, NPOL>(p, d, Zs, ps, last, c, b, j, n1_0 + c, tws);
         }
         __syncthreads();
     }
     if (p.npass == 0) __syncthreads();
+}
+
+// Stage column tile x's four-step twiddles twZ[pos][x*C + c] into shared
+// memory as [pos][c] (read once per run of spectra instead of per spectrum).
+__device__ __forceinline__ void stage_tile_twiddles(const ColParams &p, float2 *tws, int x) {
+    if (p.npass == 0) return;  // N2 == 1: no four-step twiddles
+    const int pts = p.N2 * p.C;
+    for (int e = threadIdx.x; e < pts; e += blockDim.x) {
+        const int pos = e >> p.lC, c = e & (p.C - 1);
+        tws[e] = __ldg(p.twZ + (size_t)pos * p.N1 + x * p.C + c);
+    }
 }
 
 // Widest column butterfly kernel A may use next to its register window.
@@ -195,7 +207,7 @@ __host__ __device__ constexpr int col_radix_cap(int npol, int pt, int ppt) {
 // One segment: spectra [s_beg, s_end) of the chunk for column tile x.
 template <int NPOL, int PT, int PPT>
 __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename Elem<NPOL>::T *data, int x,
-                                                   int s_beg, int s_end) {
+                                                   int s_beg, int s_end, const float2 *tws) {
     using T = typename Elem<NPOL>::T;
     constexpr int NC = 2 * NPOL;  // floats per sample
     const int C = p.C;
@@ -259,7 +271,7 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
             }
         }
         __syncthreads();
-        col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, x, s_base, nb);
+        col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, x, s_base, nb, tws);
     }
 }
 
@@ -268,13 +280,17 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     using T = typename Elem<NPOL>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
+    float2 *tws = reinterpret_cast<float2 *>(data + PT * p.N2 * p.C);  // [N2][C]
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);
         const long long base = (long long)x * p.sc;
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
-        // col_fft_store ends on a barrier, so the next segment may reuse data
-        fir_colfft_segment<NPOL, PT, PPT>(p, data, x, (int)(f - base), s_end);
+        // the barrier after the first batch's FIR orders the twiddle tile's
+        // stores before their use; col_fft_store ends on a barrier, so the
+        // next segment may overwrite data and the tile
+        stage_tile_twiddles(p, tws, x);
+        fir_colfft_segment<NPOL, PT, PPT>(p, data, x, (int)(f - base), s_end, tws);
         f = base + s_end;
     }
 }
@@ -289,6 +305,7 @@ __global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_con
     constexpr int NC = 2 * NPOL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *data = reinterpret_cast<T *>(smem_raw);  // [N2][C]
+    float2 *tws = reinterpret_cast<float2 *>(data + p.N2 * p.C);  // [N2][C]
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);
@@ -296,6 +313,7 @@ __global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_con
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
+        stage_tile_twiddles(p, tws, x);  // ordered before use by the barrier below
         long long n_pt[PPT];
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
@@ -327,7 +345,7 @@ __global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_con
             }
             __syncthreads();
             // ends on a barrier: data is free for the next spectrum
-            col_fft_store<NPOL, col_radix_cap(NPOL, 1, PPT)>(p, data, x, s, 1);
+            col_fft_store<NPOL, col_radix_cap(NPOL, 1, PPT)>(p, data, x, s, 1, tws);
         }
     }
 }
@@ -525,6 +543,136 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
             }
         }
         __syncthreads();  // acc is zeroed again by the next segment
+    }
+}
+
+// ------------------------------------------------------ kernel B, 2048 --
+// Rows of 2048 points (RB = 1; passes radix 16, 16, 8), two spectra at a
+// time. In the radix-16 passes (128 butterflies each) the block's halves
+// transform one spectrum each, synchronising on their own named barrier;
+// the radix-8 pass (256 butterflies) then runs over both spectra with every
+// thread. Thread t always computes outputs 8t .. 8t+7 of the last pass, so
+// its eight channels' accumulators live in registers. Rows are stored with
+// one pad element every 8 (pad8), which keeps all three passes' accesses
+// free of bank conflicts.
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+constexpr int kRow2048Stride = 2048 + 2048 / 8;
+
+template <int NPOL, bool KAHAN, bool FIR>
+__device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<NPOL>::T *row, int x,
+                                              int s, int ht, int half) {
+    using T = typename Elem<NPOL>::T;
+    // pass 1: block length 2048, butterfly j = ht over positions j + 128 q
+    {
+        const Pass ps = p.pass[0];
+        T v[16];
+        if constexpr (FIR) {
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = fir_sample<NPOL>(p, p.s0 + s, ht + 128 * q);
+        } else {
+            const T *zr = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = zr[ht + 128 * q];
+        }
+        Dft<16>::run(v);
+        const float2 *tw = p.twB + ps.off + ht * 15;
+#pragma unroll
+        for (int q = 1; q < 16; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+#pragma unroll
+        for (int q = 0; q < 16; q++) row[pad8(ht + 128 * q)] = v[q];
+    }
+    if (half) asm volatile("bar.sync 2, 128;" ::: "memory");
+    else asm volatile("bar.sync 1, 128;" ::: "memory");
+    // pass 2: block length 128, unit b = ht / 8, butterfly j = ht % 8
+    {
+        const Pass ps = p.pass[1];
+        const int b = ht >> 3, j = ht & 7;
+        const int base = b * 128 + j;
+        T v[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) v[q] = row[pad8(base + 8 * q)];
+        Dft<16>::run(v);
+        const float2 *tw = p.twB + ps.off + j * 15;
+#pragma unroll
+        for (int q = 1; q < 16; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+#pragma unroll
+        for (int q = 0; q < 16; q++) row[pad8(base + 8 * q)] = v[q];
+    }
+}
+
+template <int NPOL, bool KAHAN>
+__device__ __forceinline__ void row2048_last(const typename Elem<NPOL>::T *row, int t,
+                                             typename Elem<NPOL>::Acc (&acc)[8],
+                                             typename Elem<NPOL>::Acc (&comp)[8]) {
+    using T = typename Elem<NPOL>::T;
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = row[pad8(8 * t + q)];
+    Dft<8>::run(v);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if constexpr (KAHAN) {
+            if constexpr (NPOL == 2) kahan_add(acc[q], comp[q], detect4(v[q]));
+            else kahan_add(acc[q], comp[q], fmaf(v[q].x, v[q].x, v[q].y * v[q].y));
+        } else {
+            if constexpr (NPOL == 2) acc_add<2>(acc[q], v[q]);
+            else acc_add1(acc[q], v[q]);
+        }
+    }
+}
+
+template <int NPOL, bool KAHAN, bool FIR>
+__global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __grid_constant__ RowParams p) {
+    using T = typename Elem<NPOL>::T;
+    using A = typename Elem<NPOL>::Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw);  // two rows, pad8 layout
+    const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127;
+    T *own = rows + half * kRow2048Stride;
+
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);  // row tile
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+
+        A acc[8], comp[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else acc[q] = 0.f;
+            comp[q] = acc[q];
+        }
+        for (int s = s_beg; s < s_end; s += 2) {
+            const bool two = s + 1 < s_end;
+            if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR>(p, own, x, s + half, ht, half);
+            __syncthreads();
+            row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
+            if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
+            __syncthreads();  // both rows are free for the next pair
+        }
+
+        // flush: thread t holds positions 8t .. 8t+7 of row tile x
+        const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
+        A *part = reinterpret_cast<A *>(p.partial) + so;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if constexpr (KAHAN) {
+                A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
+                A a = part[q], c = pc[q];
+                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
+                else kahan_add(a, c, acc[q] - comp[q]);
+                part[q] = a;
+                pc[q] = c;
+            } else if constexpr (NPOL == 2) {
+                const float4 a = part[q];
+                part[q] = make_float4(a.x + acc[q].x, a.y + acc[q].y, a.z + acc[q].z, a.w + acc[q].w);
+            } else {
+                part[q] += acc[q];
+            }
+        }
     }
 }
 
