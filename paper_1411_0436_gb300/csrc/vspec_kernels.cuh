@@ -244,8 +244,36 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
         }
     }
 
-    for (int s_base = s_beg; s_base < s_end; s_base += PT) {
+    // PFB: each batch's PT new frames are copied into shared memory with
+    // asynchronous copies one batch ahead (double-buffered), so the FIR reads
+    // them without waiting on HBM
+    constexpr bool kStaged = PT > 1;
+    constexpr int B = 2 * NPOL;  // bytes per sample
+    unsigned char *raw = reinterpret_cast<unsigned char *>(const_cast<float2 *>(tws) + pts);  // [2][PT][pts]
+    auto stage = [&](int sb, int buf) {
+        const int nbb = min(PT, s_end - sb);
+        const int per_row = C * B / 16, per_frame = p.N2 * per_row;
+        for (int e = threadIdx.x; e < nbb * per_frame; e += blockDim.x) {
+            const int u = e / per_frame, r = e - u * per_frame;
+            const int n2 = r / per_row, ch = r - n2 * per_row;
+            const long long fr = p.s0 + sb + u + p.P - 1;  // newest frame of spectrum sb + u
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(p.in) +
+                                       (fr * p.N + n1_0 + (long long)p.N1 * n2) * B + ch * 16;
+            unsigned char *dst = raw + ((size_t)(buf * PT + u) * pts + n2 * C) * B + ch * 16;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if constexpr (kStaged) stage(s_beg, 0);
+
+    for (int s_base = s_beg, buf = 0; s_base < s_end; s_base += PT, buf ^= 1) {
         const int nb = min(PT, s_end - s_base);
+        if constexpr (kStaged) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // this batch's frames are visible; the other buffer is free
+            if (s_base + PT < s_end) stage(s_base + PT, buf ^ 1);
+        }
 #pragma unroll
         for (int u = 0; u < PT; u++) {
             if (u < nb) {
@@ -253,7 +281,15 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
                 const int snew = (u + PT - 1) % PT;
 #pragma unroll
                 for (int i = 0; i < PPT; i++) {
-                    const uint32_t wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]) ^ 0x80808080u;
+                    uint32_t wx;
+                    if constexpr (kStaged) {
+                        const unsigned char *rs = raw + ((size_t)(buf * PT + u) * pts + sm_pt[i]) * B;
+                        if constexpr (NPOL == 2) wx = *reinterpret_cast<const uint32_t *>(rs);
+                        else wx = *reinterpret_cast<const unsigned short *>(rs);
+                    } else {
+                        wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]);
+                    }
+                    wx ^= 0x80808080u;
 #pragma unroll
                     for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
                     float y[NC];
@@ -280,7 +316,7 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     using T = typename Elem<NPOL>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
-    float2 *tws = reinterpret_cast<float2 *>(data + PT * p.N2 * p.C);  // [N2][C]
+    float2 *tws = reinterpret_cast<float2 *>(data + PT * p.N2 * p.C);  // [N2][C], then (PFB) raw frames
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);
