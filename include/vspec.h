@@ -219,29 +219,35 @@ VSPEC_API vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int r
  * Launch shape of a plan. The results do not depend on it beyond FP32
  * summation order.
  *
- * Two-kernel plans (every plan except the one-pass fused one) run the
- * four-step FFT through a chunk scratch. A chunk is a run of spectra whose
- * column DFTs (kernel A) all finish before their row DFTs (kernel B) start.
- * Each launch splits its (tile, spectrum) items evenly over its CTAs; a CTA
- * that starts a run of a column tile re-reads ntaps-1 frames to fill its FIR
- * window, and each CTA of kernel B keeps its row tile's sums in a partial-sum
- * slot that is folded into d_accum once per execute.
- *   chunk_spectra    1 .. limit.chunk_spectra (a chunk longer than the plan's
+ * The two-kernel path (every plan but the one-pass fused one, and the
+ * two-kernel plan a fused plan owns) runs the four-step FFT through a chunk
+ * scratch. A chunk is a run of spectra whose column DFTs (kernel A) all
+ * finish before their row DFTs (kernel B) start. Each launch splits its
+ * (tile, spectrum) items evenly over its CTAs; a CTA that starts a run of a
+ * column tile re-reads ntaps-1 frames to fill its FIR window, and each CTA of
+ * kernel B keeps its row tile's sums in a partial-sum slot that is folded into
+ * d_accum once per execute.
+ *   chunk_spectra    1 .. limit.chunk_spectra (a chunk longer than the
  *                    scratch holds grows the scratch: the call then
- *                    synchronises the device and allocates)
+ *                    synchronises the device and allocates); 0 for a fused
+ *                    plan that owns no two-kernel plan
  *   blocks_a         CTAs per kernel-A launch: 0 (one wave, the default) or
  *                    1 .. limit.blocks_a
  *   blocks_b         CTAs per kernel-B launch: 0 (one wave) or 1 .. limit.blocks_b
- *   assist_permille  0
- * One-pass fused plans (dual-pol, 2048..32768 channels) run clusters of CTAs,
- * and a device whose SM count is not a multiple of the cluster size leaves
- * SMs idle. Such a plan owns a two-kernel plan that channelizes the last
- * assist_permille thousandths of every execute's spectra on a second stream,
- * concurrently with the clusters (none if that share is under 32 spectra).
- *   chunk_spectra, blocks_a, blocks_b  0
- *   assist_permille  0 (no assist) .. limit.assist_permille (0 where the
- *                    device leaves no SMs idle); the default balances the
- *                    two paths' measured per-SM rates
+ * One-pass fused plans (dual-pol, 2048..32768 channels) run clusters of CTAs.
+ * Except at 2048 channels they own a two-kernel plan of the same problem,
+ * which the three fields above tune, and use it in two ways:
+ *   two_kernel_from  a call with at least this many spectra runs wholly on
+ *                    the two-kernel path (faster on long calls: its work is
+ *                    spread over every SM); 0 .. INT_MAX, INT_MAX: never. The
+ *                    default is a per-size crossover measured on GB300.
+ *                    Plans without a two-kernel plan: INT_MAX; two-kernel
+ *                    plans: 0.
+ *   assist_permille  on shorter calls, the two-kernel plan channelizes the
+ *                    last assist_permille thousandths of the spectra on a
+ *                    second stream, on the SMs the clusters leave idle (none
+ *                    if that share is under 32 spectra): 0 .. limit (0 where
+ *                    the device leaves fewer than 24 SMs idle).
  * vspec_plan_get_tuning fills the current shape and the limits (either
  * pointer may be NULL). vspec_plan_set_tuning takes effect at the next
  * execute; do not call it while an execute of the plan is in flight or being
@@ -253,6 +259,7 @@ typedef struct {
     int blocks_a;
     int blocks_b;
     int assist_permille;
+    int two_kernel_from;
 } vspec_tuning;
 
 VSPEC_API vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tuning *current,

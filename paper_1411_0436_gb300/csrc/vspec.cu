@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -141,6 +142,7 @@ struct vspec_plan {
     vspec_plan *assist = nullptr;
     vspec_plan *owner = nullptr;  // the plan whose profiling records this plan's launches
     int assist_permille = 0;
+    int two_kernel_from = INT_MAX;  // fused plans: calls with this many spectra use `assist` alone
     int prio_high = 0;            // greatest stream priority of the device
     cudaStream_t assist_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_main = nullptr, ev_assist = nullptr;
@@ -268,12 +270,12 @@ vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 g
 }
 
 // Fold `slots` partial-sum slots of p->partial (and p->partial_comp in
-// compensated plans) into d_accum: with more than 16 slots, first sum each
+// compensated plans) into d_accum: with more than 48 slots, first sum each
 // group of 16 slots into its first slot, then fold the group sums.
 vspec_status launch_fold(vspec_plan *p, int slots, float *d_accum, int spectra, cudaStream_t st) {
     int groups = slots, stride = 1;
     const int N = p->N, N1 = p->N1, N2 = p->N2;
-    if (slots > 16) {
+    if (slots > 48) {
         groups = (slots + 15) / 16;
         stride = 16;
         const void *fold = p->npol == 2 ? (p->kahan ? (const void *)vspec::fold_slots_kernel<2, true>
@@ -699,13 +701,24 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
     return vspec_plan_create_ex(out, nchan, ntaps, npol, mode, window, 0u);
 }
 
-// Fused plans on a device whose SM count is not a multiple of the cluster
-// size: a two-kernel plan channelizes a share of every execute's spectra on
-// the idle SMs. The share balances the two finishing times: idle SMs at the
-// two-kernel path's per-SM rate against the clusters' SMs at the fused
-// kernel's (tuned on GB300 with 1000-spectrum dumps of 32768 channels: about
-// 0.62 of it with an 8-tap PFB, 0.70 in direct mode). With only a few idle SMs
-// the second path's fixed cost outweighs them.
+// Fused plans own a two-kernel plan of the same problem, for two uses.
+// (1) Long calls: the two-kernel path spreads its work evenly over every SM
+// and hides its memory latency better, and beyond a per-size number of
+// spectra it is the faster path; below it the fused kernel's smaller fixed
+// cost wins. The thresholds come from measurements on GB300 (time = fixed +
+// per-spectrum cost for both paths, 100 to 4000 spectra); at 2048 channels
+// the fused path is faster at every length.
+// (2) Assist: on a device whose SM count is not a multiple of the cluster
+// size, the two-kernel plan can channelize a share of a call's spectra on
+// the SMs the clusters leave idle, concurrently with the fused kernel. The
+// default share balances the two finishing times: idle SMs at the two-kernel
+// path's per-SM rate against the clusters' SMs at the fused kernel's (about
+// 0.62 of it with an 8-tap PFB, 0.70 in direct mode). With only a few idle
+// SMs the second path's fixed cost outweighs them.
+constexpr int kTwoKernelFrom[2][5] = {
+    {INT_MAX, 750, 470, 120, 0},   // PFB, nchan 2048 .. 32768
+    {INT_MAX, 2090, 720, 210, 40}  // direct
+};
 constexpr double kAssistPerSmRate = 0.62;        // PFB
 constexpr double kAssistPerSmRateDirect = 0.70;  // direct FFT
 constexpr int kAssistMinSms = 24;      // fewer idle SMs: no assist
@@ -716,7 +729,9 @@ static vspec_status setup_assist(vspec_plan *p) {
     VSPEC_CUDA(cudaDeviceGetStreamPriorityRange(nullptr, &p->prio_high));
     const int busy = p->cluster * p->nclusters;
     const int idle = p->num_sms - busy;
-    if (idle < kAssistMinSms) return VSPEC_OK;
+    const int lg = ilog2(p->N) - 11;
+    p->two_kernel_from = (lg >= 0 && lg < 5) ? kTwoKernelFrom[p->mode == VSPEC_PFB ? 0 : 1][lg] : INT_MAX;
+    if (idle < kAssistMinSms && p->two_kernel_from == INT_MAX) return VSPEC_OK;
     vspec_plan *a = nullptr;
     vspec_status st = vspec_plan_create_ex(&a, p->N, p->mode == VSPEC_PFB ? p->P : 1, p->npol,
                                            (vspec_mode)p->mode, (vspec_window)p->window, VSPEC_PLAN_TWO_KERNEL);
@@ -724,8 +739,10 @@ static vspec_status setup_assist(vspec_plan *p) {
     a->owner = p;
     p->assist = a;
     p->scratch_bytes += a->scratch_bytes;
-    const double w = idle * (p->mode == VSPEC_PFB ? kAssistPerSmRate : kAssistPerSmRateDirect);
-    p->assist_permille = (int)(1000.0 * w / (w + busy) + 0.5);
+    if (idle >= kAssistMinSms) {
+        const double w = idle * (p->mode == VSPEC_PFB ? kAssistPerSmRate : kAssistPerSmRateDirect);
+        p->assist_permille = (int)(1000.0 * w / (w + busy) + 0.5);
+    }
     VSPEC_CUDA(cudaStreamCreateWithFlags(&p->assist_st, cudaStreamNonBlocking));
     VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_main, cudaEventDisableTiming));
@@ -808,59 +825,75 @@ vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int 
         // write and a read of the intermediate when it cannot stay in L2
         int l2 = 0;
         if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, plan->device) != cudaSuccess) l2 = 0;
-        const size_t zb = (size_t)plan->sc_max * plan->N * (plan->npol == 2 ? sizeof(float4) : sizeof(float2));
-        *hbm_passes = (!plan->fused && !plan->fir_b && zb > (size_t)l2 / 2) ? 2 : 1;
+        // (a fused plan reports the two-kernel path it switches to on long calls)
+        const vspec_plan *tk = !plan->fused ? plan : plan->two_kernel_from < INT_MAX ? plan->assist : nullptr;
+        const size_t zb = tk ? (size_t)tk->sc_max * tk->N * (tk->npol == 2 ? sizeof(float4) : sizeof(float2)) : 0;
+        *hbm_passes = (tk && !tk->fir_b && zb > (size_t)l2 / 2) ? 2 : 1;
     }
     return VSPEC_OK;
 }
 
 vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tuning *current, vspec_tuning *limit) {
     if (!plan) return VSPEC_ERR_INVALID_ARG;
-    if (plan->fused) {
-        if (current) *current = vspec_tuning{0, 0, 0, plan->assist ? plan->assist_permille : 0};
-        if (limit) *limit = vspec_tuning{0, 0, 0, plan->assist ? kAssistMaxPermille : 0};
-        return VSPEC_OK;
+    const vspec_plan *tk = plan->fused ? plan->assist : plan;  // the plan that runs the two-kernel path
+    vspec_tuning cur{0, 0, 0, 0, plan->fused ? plan->two_kernel_from : 0};
+    vspec_tuning lim{0, 0, 0, 0, plan->fused && plan->assist ? INT_MAX : cur.two_kernel_from};
+    if (tk) {
+        cur.chunk_spectra = tk->sc_max;
+        cur.blocks_a = tk->blocks_a;
+        cur.blocks_b = tk->blocks_b;
+        lim.chunk_spectra = tk->sc_cap;
+        lim.blocks_a = kMaxWaves * tk->num_sms * tk->occA;
+        lim.blocks_b = kMaxWaves * tk->num_sms * tk->occB;
     }
-    const int wa = plan->num_sms * plan->occA, wb = plan->num_sms * plan->occB;
-    if (current) *current = vspec_tuning{plan->sc_max, plan->blocks_a, plan->blocks_b, 0};
-    if (limit) *limit = vspec_tuning{plan->sc_cap, kMaxWaves * wa, kMaxWaves * wb, 0};
+    if (plan->fused) {
+        const bool can_assist = plan->assist && plan->num_sms - plan->cluster * plan->nclusters >= kAssistMinSms;
+        cur.assist_permille = can_assist ? plan->assist_permille : 0;
+        lim.assist_permille = can_assist ? kAssistMaxPermille : 0;
+    }
+    if (current) *current = cur;
+    if (limit) *limit = lim;
     return VSPEC_OK;
 }
 
 vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
     if (!plan || !t) return VSPEC_ERR_INVALID_ARG;
-    if (plan->fused) {
-        const int lim = plan->assist ? kAssistMaxPermille : 0;
-        if (t->chunk_spectra != 0 || t->blocks_a != 0 || t->blocks_b != 0 || t->assist_permille < 0 ||
-            t->assist_permille > lim) {
-            g_last_error = "tuning value out of range for a one-pass fused plan";
-            return VSPEC_ERR_INVALID_ARG;
-        }
-        plan->assist_permille = t->assist_permille;
-        return VSPEC_OK;
-    }
-    if (t->chunk_spectra < 1 || t->chunk_spectra > plan->sc_cap || t->blocks_a < 0 ||
-        t->blocks_a > kMaxWaves * plan->num_sms * plan->occA || t->blocks_b < 0 ||
-        t->blocks_b > kMaxWaves * plan->num_sms * plan->occB || t->assist_permille != 0) {
-        g_last_error = "tuning value out of range";
+    vspec_tuning lim{};
+    vspec_plan_get_tuning(plan, nullptr, &lim);
+    vspec_plan *tk = plan->fused ? plan->assist : plan;
+    const bool chunk_ok = tk ? (t->chunk_spectra >= 1 && t->chunk_spectra <= lim.chunk_spectra)
+                             : t->chunk_spectra == 0;
+    const bool two_kernel_ok = plan->fused ? (plan->assist ? t->two_kernel_from >= 0 : t->two_kernel_from == INT_MAX)
+                                           : t->two_kernel_from == 0;
+    if (!chunk_ok || t->blocks_a < 0 || t->blocks_a > lim.blocks_a || t->blocks_b < 0 ||
+        t->blocks_b > lim.blocks_b || t->assist_permille < 0 || t->assist_permille > lim.assist_permille ||
+        !two_kernel_ok) {
+        g_last_error = "tuning value out of range for this plan";
         return VSPEC_ERR_INVALID_ARG;
     }
-    if (!plan->fir_b && t->chunk_spectra > plan->sc_alloc) {  // grow the chunk scratch
-        const size_t elem = plan->npol == 2 ? sizeof(float4) : sizeof(float2);
-        const size_t old_bytes = (size_t)plan->sc_alloc * plan->N * elem;
-        void *z = nullptr;
-        size_t tot = 0;
-        VSPEC_CUDA(cudaDeviceSynchronize());
-        vspec_status st = dev_alloc(&z, (size_t)t->chunk_spectra * plan->N * elem, &tot);
-        if (st != VSPEC_OK) return st;
-        cudaFree(plan->Z);
-        plan->Z = z;
-        plan->scratch_bytes += tot - old_bytes;
-        plan->sc_alloc = t->chunk_spectra;
+    if (tk) {
+        if (!tk->fir_b && t->chunk_spectra > tk->sc_alloc) {  // grow the chunk scratch
+            const size_t elem = tk->npol == 2 ? sizeof(float4) : sizeof(float2);
+            const size_t old_bytes = (size_t)tk->sc_alloc * tk->N * elem;
+            void *z = nullptr;
+            size_t tot = 0;
+            VSPEC_CUDA(cudaDeviceSynchronize());
+            vspec_status st = dev_alloc(&z, (size_t)t->chunk_spectra * tk->N * elem, &tot);
+            if (st != VSPEC_OK) return st;
+            cudaFree(tk->Z);
+            tk->Z = z;
+            tk->scratch_bytes += tot - old_bytes;
+            if (tk != plan) plan->scratch_bytes += tot - old_bytes;
+            tk->sc_alloc = t->chunk_spectra;
+        }
+        tk->sc_max = t->chunk_spectra;
+        tk->blocks_a = t->blocks_a;
+        tk->blocks_b = t->blocks_b;
     }
-    plan->sc_max = t->chunk_spectra;
-    plan->blocks_a = t->blocks_a;
-    plan->blocks_b = t->blocks_b;
+    if (plan->fused) {
+        plan->assist_permille = t->assist_permille;
+        plan->two_kernel_from = t->two_kernel_from;
+    }
     return VSPEC_OK;
 }
 
@@ -1029,6 +1062,8 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
 static vspec_status execute_one(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
                                 cudaStream_t st) {
     if (!p->fused) return run_two_kernel(p, d_in, nspectra, d_accum, st, nullptr);
+    if (p->assist && nspectra >= p->two_kernel_from)
+        return run_two_kernel(p->assist, d_in, nspectra, d_accum, st, nullptr);
     const int sa = p->assist ? (int)((long long)nspectra * p->assist_permille / 1000) : 0;
     if (sa < kAssistMinSpectra) return run_fused(p, d_in, nspectra, d_accum, st);
     // fused kernel on `st` over the first spectra, the assist plan on its own

@@ -56,7 +56,10 @@ def declared_functions() -> list:
 class VspecTuning(ctypes.Structure):
     """vspec_tuning: launch shape of the two-kernel path."""
     _fields_ = [("chunk_spectra", ctypes.c_int), ("blocks_a", ctypes.c_int), ("blocks_b", ctypes.c_int),
-                ("assist_permille", ctypes.c_int)]
+                ("assist_permille", ctypes.c_int), ("two_kernel_from", ctypes.c_int)]
+
+
+NEVER = 2 ** 31 - 1  # two_kernel_from value: never switch to the two-kernel path
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
@@ -232,7 +235,7 @@ def vspec_plan_kernel_stats(plan: int, reset: bool = False) -> list:
 
 
 def vspec_plan_get_tuning(plan: int):
-    """(current, limit) as dicts with keys chunk_spectra, blocks_a, blocks_b, assist_permille."""
+    """(current, limit) as dicts keyed by the vspec_tuning field names."""
     cur, lim = VspecTuning(), VspecTuning()
     st = load().vspec_plan_get_tuning(plan, ctypes.byref(cur), ctypes.byref(lim))
     if st != OK:
@@ -242,8 +245,8 @@ def vspec_plan_get_tuning(plan: int):
 
 
 def vspec_plan_set_tuning(plan: int, chunk_spectra: int, blocks_a: int, blocks_b: int,
-                          assist_permille: int = 0) -> None:
-    t = VspecTuning(chunk_spectra, blocks_a, blocks_b, assist_permille)
+                          assist_permille: int, two_kernel_from: int) -> None:
+    t = VspecTuning(chunk_spectra, blocks_a, blocks_b, assist_permille, two_kernel_from)
     st = load().vspec_plan_set_tuning(plan, ctypes.byref(t))
     if st != OK:
         raise VspecError(st, "vspec_plan_set_tuning")
@@ -324,8 +327,19 @@ class Plan:
     def get_tuning(self):
         return vspec_plan_get_tuning(self.handle)
 
-    def set_tuning(self, chunk_spectra: int, blocks_a: int, blocks_b: int, assist_permille: int = 0) -> None:
-        vspec_plan_set_tuning(self.handle, chunk_spectra, blocks_a, blocks_b, assist_permille)
+    def set_tuning(self, chunk_spectra: int, blocks_a: int, blocks_b: int, assist_permille: int,
+                   two_kernel_from: int) -> None:
+        vspec_plan_set_tuning(self.handle, chunk_spectra, blocks_a, blocks_b, assist_permille, two_kernel_from)
+
+    def tune(self, **changes) -> dict:
+        """Change some fields of the launch shape, keep the others; returns the new shape."""
+        cur, _ = self.get_tuning()
+        unknown = set(changes) - set(cur)
+        if unknown:
+            raise KeyError(f"unknown tuning fields {sorted(unknown)}")
+        cur.update(changes)
+        self.set_tuning(**cur)
+        return cur
 
     def close(self) -> None:
         if self.handle:

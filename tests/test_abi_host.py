@@ -63,6 +63,6 @@ def test_null_arguments_are_rejected(lib):
 
 
 def test_tuning_rejects_null_arguments(lib):
-    t = vspec.VspecTuning(1, 0, 1, 0)
+    t = vspec.VspecTuning(1, 0, 1, 0, 0)
     assert lib.vspec_plan_get_tuning(None, None, None) == vspec.ERR_INVALID_ARG
     assert lib.vspec_plan_set_tuning(None, ctypes.byref(t)) == vspec.ERR_INVALID_ARG

@@ -22,9 +22,11 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def run_gpu(bank: Bank, x: np.ndarray, repeat: int = 1, flags: int = 0) -> np.ndarray:
+def run_gpu(bank: Bank, x: np.ndarray, repeat: int = 1, flags: int = 0, tuning=None) -> np.ndarray:
     from paper_1411_0436_gb300.vspec import Plan
     with Plan(bank.nchan, bank.ntaps, bank.npol, bank.mode, bank.window, flags) as plan:
+        if tuning:
+            plan.tune(**tuning)
         d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
         acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
         for _ in range(repeat):
@@ -89,7 +91,10 @@ def test_matches_oracle(oracle_mod, cfg):
     x = workloads.generate(bank, 1000 + n + p)
     o = run_oracle(oracle_mod, bank, x)
     assert_close(run_gpu(bank, x), o, what=str(cfg))
-    if fused_applies(n, p, npol, mode):  # also the general path at the same size
+    if fused_applies(n, p, npol, mode):  # the one-pass fused path alone, and the general path
+        from paper_1411_0436_gb300.vspec import NEVER
+        assert_close(run_gpu(bank, x, tuning={"two_kernel_from": NEVER, "assist_permille": 0}), o,
+                     what=f"{cfg} fused")
         assert_close(run_gpu(bank, x, flags=PLAN_TWO_KERNEL), o, what=f"{cfg} two-kernel")
 
 
@@ -183,10 +188,12 @@ def test_error_paths_on_device():
         assert sb > 0 and hp == 1  # one-row transform: FIR, FFT and detection in one kernel
     with vspec.Plan(131072, 8, 2, PFB, WIN_HANN) as plan:
         assert plan.info()[1] == 2  # 512 MiB chunk scratch: the intermediate goes through HBM
-        plan.set_tuning(16, 0, 0)   # 32 MiB chunks stay in L2
+        plan.tune(chunk_spectra=16)  # 32 MiB chunks stay in L2
         assert plan.info()[1] == 1
     with vspec.Plan(32768, 8, 2, PFB, WIN_HANN) as plan:
-        assert plan.info()[1] == 1  # one-pass fused path
+        assert plan.info()[1] == 2  # long calls switch to the two-kernel path
+        plan.tune(two_kernel_from=vspec.NEVER)
+        assert plan.info()[1] == 1  # one-pass fused path only
 
 
 @pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (1024, 8, 1, PFB, WIN_HANN, 70),
@@ -364,7 +371,7 @@ def test_launch_shapes_match_oracle(oracle_mod, cfg):
                   (lim["chunk_spectra"], 7, lim["blocks_b"]), (lim["chunk_spectra"], 0, 1),
                   (cur["chunk_spectra"], lim["blocks_a"], 0)]
         for chunk, ba, bb in shapes:
-            plan.set_tuning(chunk, ba, bb)
+            plan.tune(chunk_spectra=chunk, blocks_a=ba, blocks_b=bb)
             acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
             plan.execute(d_in, s, acc)
             torch.cuda.synchronize()
@@ -373,25 +380,63 @@ def test_launch_shapes_match_oracle(oracle_mod, cfg):
 
 
 def test_tuning_limits():
-    from paper_1411_0436_gb300.vspec import Plan, VspecError
+    from paper_1411_0436_gb300.vspec import NEVER, Plan, VspecError
     import paper_1411_0436_gb300.vspec as V
-    with Plan(65536, 8, 2, PFB, WIN_HANN) as plan:
+
+    def rejected(plan, **bad):
+        before = plan.get_tuning()[0]
+        with pytest.raises(VspecError) as e:
+            plan.tune(**bad)
+        assert e.value.status == V.ERR_INVALID_ARG
+        assert plan.get_tuning()[0] == before  # a rejected shape changes nothing
+
+    with Plan(65536, 8, 2, PFB, WIN_HANN) as plan:  # two-kernel plan
         cur, lim = plan.get_tuning()
-        assert lim["assist_permille"] == 0
-        for bad in [(0, 0, 0), (lim["chunk_spectra"] + 1, 0, 0), (1, -1, 0), (1, lim["blocks_a"] + 1, 0),
-                    (1, 0, -1), (1, 0, lim["blocks_b"] + 1), (1, 0, 0, 5)]:
-            with pytest.raises(VspecError) as e:
-                plan.set_tuning(*bad)
-            assert e.value.status == V.ERR_INVALID_ARG
-        assert plan.get_tuning()[0] == cur  # a rejected shape changes nothing
-    with Plan(32768, 8, 2, PFB, WIN_HANN) as plan:  # one-pass fused plan
+        assert cur["two_kernel_from"] == 0 and lim["assist_permille"] == 0
+        for bad in [dict(chunk_spectra=0), dict(chunk_spectra=lim["chunk_spectra"] + 1), dict(blocks_a=-1),
+                    dict(blocks_a=lim["blocks_a"] + 1), dict(blocks_b=-1), dict(blocks_b=lim["blocks_b"] + 1),
+                    dict(assist_permille=5), dict(two_kernel_from=7)]:
+            rejected(plan, **bad)
+    with Plan(32768, 8, 2, PFB, WIN_HANN) as plan:  # fused plan owning a two-kernel plan
         cur, lim = plan.get_tuning()
-        assert cur["chunk_spectra"] == cur["blocks_a"] == cur["blocks_b"] == 0
+        assert cur["chunk_spectra"] >= 1 and lim["two_kernel_from"] == NEVER
         assert 0 <= cur["assist_permille"] <= lim["assist_permille"] <= 1000
-        for bad in [(1, 0, 0, 0), (0, 0, 1, 0), (0, 0, 0, -1), (0, 0, 0, lim["assist_permille"] + 1)]:
-            with pytest.raises(VspecError) as e:
-                plan.set_tuning(*bad)
-            assert e.value.status == V.ERR_INVALID_ARG
+        for bad in [dict(chunk_spectra=0), dict(assist_permille=-1),
+                    dict(assist_permille=lim["assist_permille"] + 1), dict(two_kernel_from=-1)]:
+            rejected(plan, **bad)
+        plan.tune(two_kernel_from=NEVER, assist_permille=0)
+    with Plan(2048, 8, 2, PFB, WIN_HANN) as plan:  # fused, no two-kernel plan
+        cur, lim = plan.get_tuning()
+        assert cur == {"chunk_spectra": 0, "blocks_a": 0, "blocks_b": 0, "assist_permille": 0,
+                       "two_kernel_from": NEVER}
+        rejected(plan, two_kernel_from=100)
+        rejected(plan, chunk_spectra=4)
+
+
+@pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 150), (8192, 1, 2, DIRECT, WIN_RECT, 900)],
+                         ids=lambda c: f"N{c[0]}_m{c[3]}_S{c[5]}")
+def test_fused_plan_switches_to_two_kernel_path(oracle_mod, cfg):
+    """A fused plan runs a call wholly on its two-kernel plan from
+    two_kernel_from spectra on, and on the cluster kernel below; both give
+    the oracle's spectrum and the profiling records show which path ran."""
+    from paper_1411_0436_gb300.vspec import NEVER, Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3, tones=(Tone(25.0, n * 0.3 + 0.4, (0, 1)),))
+    x = workloads.generate(bank, 55 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
+    with Plan(n, p, npol, mode, win) as plan:
+        for threshold, two_kernel in ((s, True), (s + 1, False), (0, True), (NEVER, False)):
+            plan.tune(two_kernel_from=threshold, assist_permille=0)
+            plan.set_profiling(True)
+            acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+            plan.execute(d_in, s, acc)
+            torch.cuda.synchronize()
+            stats = {r[0]: r for r in plan.kernel_stats()}
+            plan.set_profiling(False)
+            assert_close(acc.cpu().numpy().astype(np.float64).reshape(n, 4), o, what=f"{cfg} from {threshold}")
+            assert (stats["fir_colfft"][2] == s) == two_kernel
+            assert (stats["fused_channelize"][2] == s) == (not two_kernel)
 
 
 @pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (32768, 1, 2, DIRECT, WIN_HAMMING, 233),
@@ -403,7 +448,7 @@ def test_fused_assist_shares_match_oracle(oracle_mod, cfg):
     concurrent two-kernel pass on the idle SMs; every split (none, the
     default, half, the maximum) gives the oracle's spectrum, and the
     profiling records cover both paths' kernels."""
-    from paper_1411_0436_gb300.vspec import Plan
+    from paper_1411_0436_gb300.vspec import NEVER, Plan
     n, p, npol, mode, win, s = cfg
     bank = Bank(n, p, npol, mode, win, s, sigma=20.0, rho=0.3, tones=(Tone(25.0, n * 0.3 + 0.4, (0, 1)),))
     x = workloads.generate(bank, 99 + n)
@@ -412,7 +457,7 @@ def test_fused_assist_shares_match_oracle(oracle_mod, cfg):
     with Plan(n, p, npol, mode, win) as plan:
         cur, lim = plan.get_tuning()
         for share in sorted({0, cur["assist_permille"], min(500, lim["assist_permille"]), lim["assist_permille"]}):
-            plan.set_tuning(0, 0, 0, share)
+            plan.tune(assist_permille=share, two_kernel_from=NEVER)
             plan.set_profiling(True)
             acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
             plan.execute(d_in, s, acc)
