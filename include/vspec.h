@@ -160,17 +160,35 @@ VSPEC_API vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int n
  *          compute; pageable memory works but serialises.
  *   h_out  host float[nchan * 4] (npol == 2) or float[nchan]: overwritten
  *          with the accumulated spectra of these nspectra spectra.
- * The spectra are processed in chunks of about 32 MiB of input: a plan-owned
- * copy stream fills one of two device staging buffers while a plan-owned
- * compute stream channelizes the other. All work starts after the work
- * already queued on `stream`, and `stream` waits for the final copy, so the
- * caller synchronises `stream` before reading h_out. The first call on a plan
- * allocates the staging buffers (two chunks of input plus one accumulator)
- * and creates the streams. Calls on one plan must be serialised.
- * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
+ * Two ways to bring the input over, chosen by vspec_plan_set_host_mode:
+ *   staged  chunks of about 32 MiB of input: a plan-owned copy stream fills
+ *           one of two device staging buffers while a plan-owned compute
+ *           stream channelizes the other;
+ *   mapped  pinned host memory that the device can address (any cudaHostAlloc
+ *           or cudaHostRegister buffer on a unified-address system) is read
+ *           by the kernels directly, once per byte, over the host link: no
+ *           staging copy at all.
+ * Auto maps when cudaPointerGetAttributes reports h_in as pinned host memory
+ * with a device address, and stages otherwise. The default is staged: on
+ * GB300 both ways run at the host link's rate (about 170 GB/s of input),
+ * staged a little faster on short calls. All work starts
+ * after the work already queued on `stream`, and `stream` waits for the final
+ * copy, so the caller synchronises `stream` before reading h_out. The first
+ * call on a plan allocates the staging buffers (two chunks of input plus one
+ * accumulator) and creates the streams. Calls on one plan must be serialised.
+ * Errors: VSPEC_ERR_INVALID_ARG (also: mapped mode with an h_in the device
+ * cannot address), VSPEC_ERR_ALIGNMENT (mapped h_in not 16-byte aligned),
+ * VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
  */
 VSPEC_API vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspectra,
                                           float *h_out, void *stream);
+
+#define VSPEC_HOST_AUTO 0   /* map pinned device-addressable input, else stage */
+#define VSPEC_HOST_STAGED 1 /* always copy through the staging buffers */
+#define VSPEC_HOST_MAPPED 2 /* always read the host input directly */
+
+/* Select how vspec_execute_host brings the input over (VSPEC_HOST_*). */
+VSPEC_API vspec_status vspec_plan_set_host_mode(vspec_plan *plan, int mode);
 
 /*
  * Dump the accumulator (§4, "copy output to host") and clear it.

@@ -165,6 +165,7 @@ struct vspec_plan {
     std::vector<cudaEvent_t> event_pool;
     // host-input pipeline (vspec_execute_host), created on first use
     bool host_ready = false;
+    int host_mode = VSPEC_HOST_STAGED;
     cudaStream_t copy_st = nullptr, comp_st = nullptr;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
@@ -1154,6 +1155,30 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     VSPEC_CUDA(cudaStreamWaitEvent(p->copy_st, p->ev_start, 0));
     VSPEC_CUDA(cudaStreamWaitEvent(p->comp_st, p->ev_start, 0));
     VSPEC_CUDA(cudaMemsetAsync(p->hacc, 0, out_bytes, p->comp_st));
+
+    // mapped input: the kernels read the pinned host buffer through its
+    // device address
+    const int8_t *mapped = nullptr;
+    if (p->host_mode != VSPEC_HOST_STAGED) {
+        cudaPointerAttributes attr{};
+        if (cudaPointerGetAttributes(&attr, h_in) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            attr.devicePointer != nullptr)
+            mapped = static_cast<const int8_t *>(attr.devicePointer);
+        else
+            cudaGetLastError();  // clear a lookup failure on unregistered memory
+        if (!mapped && p->host_mode == VSPEC_HOST_MAPPED) {
+            g_last_error = "vspec_execute_host: h_in is not pinned host memory the device can address";
+            return VSPEC_ERR_INVALID_ARG;
+        }
+    }
+    if (mapped) {
+        vspec_status r = vspec_execute(p, mapped, nspectra, p->hacc, (void *)p->comp_st);
+        if (r != VSPEC_OK) return r;
+        VSPEC_CUDA(cudaMemcpyAsync(h_out, p->hacc, out_bytes, cudaMemcpyDeviceToHost, p->comp_st));
+        VSPEC_CUDA(cudaEventRecord(p->ev_done, p->comp_st));
+        VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
+        return VSPEC_OK;
+    }
     const int chunk = p->stage_spectra;
     int k = 0;
     for (int s0 = 0; s0 < nspectra; s0 += chunk, k++) {
@@ -1172,6 +1197,12 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     VSPEC_CUDA(cudaMemcpyAsync(h_out, p->hacc, out_bytes, cudaMemcpyDeviceToHost, p->comp_st));
     VSPEC_CUDA(cudaEventRecord(p->ev_done, p->comp_st));
     VSPEC_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_set_host_mode(vspec_plan *plan, int mode) {
+    if (!plan || mode < VSPEC_HOST_AUTO || mode > VSPEC_HOST_MAPPED) return VSPEC_ERR_INVALID_ARG;
+    plan->host_mode = mode;
     return VSPEC_OK;
 }
 

@@ -252,10 +252,11 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
     unsigned char *raw = reinterpret_cast<unsigned char *>(const_cast<float2 *>(tws) + pts);  // [2][PT][pts]
     auto stage = [&](int sb, int buf) {
         const int nbb = min(PT, s_end - sb);
-        const int per_row = C * B / 16, per_frame = p.N2 * per_row;
-        for (int e = threadIdx.x; e < nbb * per_frame; e += blockDim.x) {
-            const int u = e / per_frame, r = e - u * per_frame;
-            const int n2 = r / per_row, ch = r - n2 * per_row;
+        // 16-byte chunks: per_row = C * B / 16 per tile row, N2 rows per frame
+        const int lrow = p.lC + (NPOL == 2 ? 2 : 1) - 4, lframe = lrow + p.lN2;
+        for (int e = threadIdx.x; e < (nbb << lframe); e += blockDim.x) {
+            const int u = e >> lframe, r = e & ((1 << lframe) - 1);
+            const int n2 = r >> lrow, ch = r & ((1 << lrow) - 1);
             const long long fr = p.s0 + sb + u + p.P - 1;  // newest frame of spectrum sb + u
             const unsigned char *src = reinterpret_cast<const unsigned char *>(p.in) +
                                        (fr * p.N + n1_0 + (long long)p.N1 * n2) * B + ch * 16;

@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_get_tuning.restype = i
         lib.vspec_plan_set_tuning.argtypes = [vp, ctypes.POINTER(VspecTuning)]
         lib.vspec_plan_set_tuning.restype = i
+        lib.vspec_plan_set_host_mode.argtypes = [vp, i]
+        lib.vspec_plan_set_host_mode.restype = i
         lib.vspec_status_string.argtypes = [i]
         lib.vspec_status_string.restype = cp
         lib.vspec_last_error.argtypes = []
@@ -252,6 +254,15 @@ def vspec_plan_set_tuning(plan: int, chunk_spectra: int, blocks_a: int, blocks_b
         raise VspecError(st, "vspec_plan_set_tuning")
 
 
+HOST_AUTO, HOST_STAGED, HOST_MAPPED = 0, 1, 2
+
+
+def vspec_plan_set_host_mode(plan: int, mode: int) -> None:
+    st = load().vspec_plan_set_host_mode(plan, mode)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_set_host_mode")
+
+
 def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, window: int,
                           nspectra: int, d_accum, stream=None) -> None:
     """Allocation-free channelization (no plan, no cudaMalloc); see include/vspec.h."""
@@ -305,6 +316,9 @@ class Plan:
     def execute_host(self, h_in, nspectra: int, h_out, stream=None) -> None:
         """Host input -> host output with overlapped copies (see vspec_execute_host)."""
         vspec_execute_host(self.handle, h_in, nspectra, h_out, stream)
+
+    def set_host_mode(self, mode: int) -> None:
+        vspec_plan_set_host_mode(self.handle, mode)
 
     def dump(self, d_accum, h_out=None, stream=None) -> None:
         vspec_dump(self.handle, d_accum, h_out, stream)

@@ -199,24 +199,42 @@ def test_error_paths_on_device():
 @pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 300), (1024, 8, 1, PFB, WIN_HANN, 70),
                                  (131072, 1, 2, DIRECT, WIN_RECT, 40)])
 def test_execute_host_pipeline_matches_oracle(oracle_mod, cfg):
-    """Host input -> host output with overlapped chunked copies (the paper's
-    copy / compute / copy loop): several chunks, and a second call that must
-    overwrite, not add to, the output."""
-    from paper_1411_0436_gb300.vspec import Plan
+    """Host input -> host output (the paper's copy / compute / copy loop), in
+    every input mode: staged chunks with overlapped copies, pinned input read
+    directly by the kernels (mapped), the automatic choice for pinned and for
+    pageable input; a second call must overwrite, not add to, the output."""
+    from paper_1411_0436_gb300.vspec import HOST_AUTO, HOST_MAPPED, HOST_STAGED, Plan
     n, p, npol, mode, win, s = cfg
     bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0,
                 tones=(Tone(25.0, n * 0.21 + 0.3, (0,)),))
     x = workloads.generate(bank, 77 + n)
     o = run_oracle(oracle_mod, bank, x)
+    pinned = torch.from_numpy(x.view(np.uint8).reshape(-1)).pin_memory()
+    pageable = np.ascontiguousarray(x.view(np.uint8).reshape(-1))
     with Plan(n, p, npol, mode, win) as plan:
-        h_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).pin_memory()
         h_out = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
-        for _ in range(2):
-            h_out.fill_(123.0)
-            plan.execute_host(h_in, s, h_out)
-            torch.cuda.synchronize()
-            got = h_out.numpy().astype(np.float64)
-            assert_close(got.reshape(o.shape), o, what=f"{cfg} host pipeline")
+        for host_mode, h_in in ((HOST_STAGED, pinned), (HOST_MAPPED, pinned), (HOST_AUTO, pinned),
+                                (HOST_AUTO, pageable)):
+            plan.set_host_mode(host_mode)
+            for _ in range(2):
+                h_out.fill_(123.0)
+                plan.execute_host(h_in, s, h_out)
+                torch.cuda.synchronize()
+                got = h_out.numpy().astype(np.float64)
+                assert_close(got.reshape(o.shape), o, what=f"{cfg} host mode {host_mode}")
+
+
+def test_mapped_host_mode_rejects_pageable_input():
+    from paper_1411_0436_gb300 import vspec
+    with vspec.Plan(4096, 8, 2, PFB, WIN_HANN) as plan:
+        plan.set_host_mode(vspec.HOST_MAPPED)
+        h_in = np.zeros(4096 * 4 * 9, np.uint8)  # pageable
+        h_out = np.zeros(4096 * 4, np.float32)
+        with pytest.raises(vspec.VspecError) as e:
+            plan.execute_host(h_in, 2, h_out)
+        assert e.value.status == vspec.ERR_INVALID_ARG
+        with pytest.raises(vspec.VspecError):
+            plan.set_host_mode(3)
 
 
 def test_batch_graph_matches_single_banks(oracle_mod):
