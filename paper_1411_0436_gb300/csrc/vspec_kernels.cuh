@@ -35,7 +35,7 @@ template <> struct Elem<1> {
     using Acc = float;    // XX
 };
 template <> struct Elem<2> {
-    using T = float4;     // both polarisations of one sample or channel
+    using T = P2;         // both polarisations of one sample or channel, packed
     using Acc = float4;   // XX, YY, Re XY*, Im XY*
 };
 
@@ -302,7 +302,7 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
                         for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
                     }
                     T *d = data + u * pts + sm_pt[i];
-                    if constexpr (NPOL == 2) *d = make_float4(y[0], y[1], y[2], y[3]);
+                    if constexpr (NPOL == 2) *d = make_p2(y[0], y[1], y[2], y[3]);
                     else *d = make_float2(y[0], y[1]);
                 }
             }
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_con
 #pragma unroll
             for (int i = 0; i < PPT; i++) {
                 T *d = data + threadIdx.x + i * blockDim.x;
-                if constexpr (NPOL == 2) *d = make_float4(y[i][0], y[i][1], y[i][2], y[i][3]);
+                if constexpr (NPOL == 2) *d = make_p2(y[i][0], y[i][1], y[i][2], y[i][3]);
                 else *d = make_float2(y[i][0], y[i][1]);
             }
             __syncthreads();
@@ -401,6 +401,18 @@ template <int NPOL> __device__ __forceinline__ void acc_add(float4 &a, float4 v)
     a.y += yy;
     a.z += re;
     a.w += im;
+}
+// the same from the packed form: (XX, YY) is one paired operation
+__device__ __forceinline__ float4 detect4(P2 v) {
+    const float2 p = __ffma2_rn(v.re, v.re, __fmul2_rn(v.im, v.im));  // (|X|^2, |Y|^2)
+    return make_float4(p.x, p.y, fmaf(v.re.x, v.re.y, v.im.x * v.im.y), fmaf(v.im.x, v.re.y, -(v.re.x * v.im.y)));
+}
+template <int NPOL> __device__ __forceinline__ void acc_add(float4 &a, P2 v) {
+    const float4 d = detect4(v);
+    a.x += d.x;
+    a.y += d.y;
+    a.z += d.z;
+    a.w += d.w;
 }
 __device__ __forceinline__ void acc_add1(float &a, float2 v) { a += fmaf(v.x, v.x, v.y * v.y); }
 
@@ -452,7 +464,7 @@ __device__ __forceinline__ typename Elem<NPOL>::T fir_sample(const RowParams &p,
 #pragma unroll
         for (int k = 0; k < NC; k++) a[k] = fmaf(c, unpack_byte(w, k), a[k]);
     }
-    if constexpr (NPOL == 2) return make_float4(a[0], a[1], a[2], a[3]);
+    if constexpr (NPOL == 2) return make_p2(a[0], a[1], a[2], a[3]);
     else return make_float2(a[0], a[1]);
 }
 

@@ -32,9 +32,9 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     extern __shared__ __align__(128) unsigned char smem_tc[];
     unsigned char *a0hi = smem_tc, *a0lo = a0hi + kAPart, *a1hi = a0lo + kAPart, *a1lo = a1hi + kAPart;
     unsigned char *bhi = a1lo + kAPart, *blo = bhi + kBPart;
-    float4 *data = reinterpret_cast<float4 *>(smem_tc + kTcSmemOps);   // one row, padded
+    P2 *data = reinterpret_cast<P2 *>(smem_tc + kTcSmemOps);   // one row, padded
     const int rowstride = kTcN1 + kTcN1 / 16;
-    float4 *acc = data + rowstride;
+    float4 *acc = reinterpret_cast<float4 *>(data + rowstride);
     float4 *comp = acc + kTcN1;  // compensation (compensated plans only)
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -80,14 +80,14 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
         __syncthreads();
 
         for (int s = s_beg; s < s_end && ok; s++, k++) {
-            const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)x * kTcN1;
+            const P2 *zr = reinterpret_cast<const P2 *>(p.Z) + (size_t)s * p.N + (size_t)x * kTcN1;
             if (tid < kRows) {
-                float2 v0[16], v1[16];
+                float2 v0[16], v1[16];  // X and Y as (re, im)
 #pragma unroll
                 for (int r = 0; r < 16; r++) {
-                    const float4 e = zr[tid + kRows * r];
-                    v0[r] = make_float2(e.x, e.y);
-                    v1[r] = make_float2(e.z, e.w);
+                    const P2 e = zr[tid + kRows * r];
+                    v0[r] = make_float2(e.re.x, e.im.x);
+                    v1[r] = make_float2(e.re.y, e.im.y);
                 }
                 stage_row(a0hi, a0lo, tid, v0);
                 stage_row(a1hi, a1lo, tid, v1);
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
                 const float2 *tw = p.twB + p0.off + j * 15;
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
-                    float4 vq = make_float4(d0[2 * q], d0[2 * q + 1], d1[2 * q], d1[2 * q + 1]);
+                    P2 vq = make_p2(d0[2 * q], d0[2 * q + 1], d1[2 * q], d1[2 * q + 1]);
                     if (q > 0) vq = cmul(vq, __ldg(tw + q - 1));
                     data[pad16(j + kRows * q)] = vq;
                 }

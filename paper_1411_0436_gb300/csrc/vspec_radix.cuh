@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace vspec {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -30,6 +32,35 @@ __device__ __forceinline__ float4 cmul(float4 a, float2 w) {
 // multiplication by -i: (re, im) -> (im, -re)
 __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
 __device__ __forceinline__ float4 cmul_mi(float4 a) { return make_float4(a.y, -a.x, a.w, -a.z); }
+
+// a + (-i) b and a - (-i) b
+template <typename T> __device__ __forceinline__ T add_mi(T a, T b) { return cadd(a, cmul_mi(b)); }
+template <typename T> __device__ __forceinline__ T sub_mi(T a, T b) { return csub(a, cmul_mi(b)); }
+
+// Both polarisations of one complex value, packed for the paired FP32
+// instructions of sm_100 and later (FADD2 / FMUL2 / FFMA2): re = (X.re, Y.re),
+// im = (X.im, Y.im). Every DFT step applies the same operation with the same
+// twiddle to X and Y, so each step is one paired instruction for both. In
+// memory a P2 is 16 bytes: X.re, Y.re, X.im, Y.im.
+struct __align__(16) P2 {
+    float2 re, im;
+};
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one fused multiply-add with -1 (exactly the rounded difference)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ P2 make_p2(float xr, float xi, float yr, float yi) {
+    return P2{make_float2(xr, yr), make_float2(xi, yi)};
+}
+__device__ __forceinline__ P2 cadd(P2 a, P2 b) { return P2{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ P2 csub(P2 a, P2 b) { return P2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// (re + i im) (w.x + i w.y) for both polarisations
+__device__ __forceinline__ P2 cmul(P2 a, float2 w) {
+    return P2{__ffma2_rn(a.im, dup2(-w.y), __fmul2_rn(a.re, dup2(w.x))),
+              __ffma2_rn(a.im, dup2(w.x), __fmul2_rn(a.re, dup2(w.y)))};
+}
+template <> __device__ __forceinline__ P2 add_mi<P2>(P2 a, P2 b) { return P2{add2(a.re, b.im), sub2(a.im, b.re)}; }
+template <> __device__ __forceinline__ P2 sub_mi<P2>(P2 a, P2 b) { return P2{sub2(a.re, b.im), add2(a.im, b.re)}; }
 
 // multiplication by a twiddle given as compile-time constants (c, s): c + i s
 template <typename T> __device__ __forceinline__ T cmulc(T a, float c, float s) {
@@ -75,21 +106,31 @@ template <> struct Dft<2> {
 template <> struct Dft<4> {
     template <typename T> __device__ __forceinline__ static void run(T (&v)[4]) {
         T a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-        T c = cadd(v[1], v[3]), d = cmul_mi(csub(v[1], v[3]));
+        T c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
         v[0] = cadd(a, c);
         v[2] = csub(a, c);
-        v[1] = cadd(b, d);
-        v[3] = csub(b, d);
+        v[1] = add_mi(b, d);  // b + (-i) d
+        v[3] = sub_mi(b, d);
     }
 };
 
 template <int R> struct DftSplit {
+    // outputs Q and Q + R/2 from the even and odd half-length DFTs
+    template <int Q, typename T>
+    __device__ __forceinline__ static void combine_one(T (&v)[R], const T (&e)[R / 2], const T (&o)[R / 2]) {
+        if constexpr ((R == 8 ? 2 * Q : Q) == 4) {  // twiddle -i
+            v[Q] = add_mi(e[Q], o[Q]);
+            v[Q + R / 2] = sub_mi(e[Q], o[Q]);
+        } else {
+            const T t = twiddle_const<R, Q>(o[Q]);
+            v[Q] = cadd(e[Q], t);
+            v[Q + R / 2] = csub(e[Q], t);
+        }
+    }
     template <typename T, int... Q>
     __device__ __forceinline__ static void combine(T (&v)[R], T (&e)[R / 2], T (&o)[R / 2],
                                                    std::integer_sequence<int, Q...>) {
-        ((o[Q] = twiddle_const<R, Q>(o[Q])), ...);
-        ((v[Q] = cadd(e[Q], o[Q])), ...);
-        ((v[Q + R / 2] = csub(e[Q], o[Q])), ...);
+        (combine_one<Q>(v, e, o), ...);
     }
     template <typename T> __device__ __forceinline__ static void run(T (&v)[R]) {
         T e[R / 2], o[R / 2];
