@@ -101,6 +101,18 @@ __device__ __forceinline__ float unpack_byte(uint32_t wx, int i) {
     return __int_as_float(__byte_perm(wx, 0x4B000000u, 0x7540u + i)) - 8388736.0f;
 }
 
+// Both polarisations of one dual-pol input word (already ^ 0x80808080) as
+// P2: the real parts are bytes 0 and 2, the imaginary parts bytes 1 and 3.
+// The bias is removed with one paired add per part; exact as above.
+__device__ __forceinline__ P2 unpack_p2(uint32_t wx) {
+    const float2 bias = make_float2(-8388736.0f, -8388736.0f);
+    const float2 r = make_float2(__int_as_float(__byte_perm(wx, 0x4B000000u, 0x7540u)),
+                                 __int_as_float(__byte_perm(wx, 0x4B000000u, 0x7542u)));
+    const float2 i = make_float2(__int_as_float(__byte_perm(wx, 0x4B000000u, 0x7541u)),
+                                 __int_as_float(__byte_perm(wx, 0x4B000000u, 0x7543u)));
+    return P2{__fadd2_rn(r, bias), __fadd2_rn(i, bias)};
+}
+
 template <int NPOL> __device__ __forceinline__ uint32_t load_raw(const int8_t *in, long long m);
 template <> __device__ __forceinline__ uint32_t load_raw<2>(const int8_t *in, long long m) {
     return __ldg(reinterpret_cast<const unsigned int *>(in) + m);
@@ -215,9 +227,13 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
     const int n1_0 = x * C;
     const int D = PT - p.P;  // leading zero taps
 
+    // dual-pol with few window registers: the FIR runs on paired FP32
+    // instructions (coefficients duplicated into register pairs)
+    constexpr bool kPacked = NPOL == 2 && PPT * PT <= 8;
     long long n_pt[PPT];
     int sm_pt[PPT];
     float cf[PPT][PT];
+    float2 cf2[kPacked ? PPT : 1][kPacked ? PT : 1];
 #pragma unroll
     for (int i = 0; i < PPT; i++) {
         const int idx = threadIdx.x + i * blockDim.x;  // = n2 * C + c
@@ -225,12 +241,15 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
         n_pt[i] = n1_0 + c + (long long)p.N1 * n2;
         sm_pt[i] = idx;
 #pragma unroll
-        for (int t = 0; t < PT; t++)
+        for (int t = 0; t < PT; t++) {
             cf[i][t] = (t >= D) ? __ldg(p.coef + (size_t)(t - D) * p.N + n_pt[i]) : 0.0f;
+            if constexpr (kPacked) cf2[i][t] = dup2(cf[i][t]);
+        }
     }
 
     // Slot (s - s_beg + t) % PT of the window holds frame s + t - D.
-    float win[PPT][PT][NC];
+    float win[kPacked ? 1 : PPT][kPacked ? 1 : PT][NC];
+    P2 win2[kPacked ? PPT : 1][kPacked ? PT : 1];
     const long long sabs = p.s0 + s_beg;
 #pragma unroll
     for (int t = 0; t < PT - 1; t++) {
@@ -239,8 +258,12 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
             const uint32_t wx = load_raw<NPOL>(p.in, f * p.N + n_pt[i]) ^ 0x80808080u;
+            if constexpr (kPacked) {
+                win2[i][t] = unpack_p2(wx);
+            } else {
 #pragma unroll
-            for (int k = 0; k < NC; k++) win[i][t][k] = unpack_byte(wx, k);
+                for (int k = 0; k < NC; k++) win[i][t][k] = unpack_byte(wx, k);
+            }
         }
     }
 
@@ -291,19 +314,32 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
                         wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]);
                     }
                     wx ^= 0x80808080u;
-#pragma unroll
-                    for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
-                    float y[NC];
-#pragma unroll
-                    for (int k = 0; k < NC; k++) y[k] = cf[i][0] * win[i][u % PT][k];
-#pragma unroll
-                    for (int t = 1; t < PT; t++) {
-#pragma unroll
-                        for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
-                    }
                     T *d = data + u * pts + sm_pt[i];
-                    if constexpr (NPOL == 2) *d = make_p2(y[0], y[1], y[2], y[3]);
-                    else *d = make_float2(y[0], y[1]);
+                    if constexpr (kPacked) {
+                        win2[i][snew] = unpack_p2(wx);
+                        const P2 &w0 = win2[i][u % PT];
+                        P2 y{__fmul2_rn(cf2[i][0], w0.re), __fmul2_rn(cf2[i][0], w0.im)};
+#pragma unroll
+                        for (int t = 1; t < PT; t++) {
+                            const P2 &wt = win2[i][(u + t) % PT];
+                            y.re = __ffma2_rn(cf2[i][t], wt.re, y.re);
+                            y.im = __ffma2_rn(cf2[i][t], wt.im, y.im);
+                        }
+                        *d = y;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
+                        float y[NC];
+#pragma unroll
+                        for (int k = 0; k < NC; k++) y[k] = cf[i][0] * win[i][u % PT][k];
+#pragma unroll
+                        for (int t = 1; t < PT; t++) {
+#pragma unroll
+                            for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
+                        }
+                        if constexpr (NPOL == 2) *d = make_p2(y[0], y[1], y[2], y[3]);
+                        else *d = make_float2(y[0], y[1]);
+                    }
                 }
             }
         }
