@@ -21,6 +21,7 @@
 // digit-reversal maps and only the final scatter into channel order uses them.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include "vspec_radix.cuh"
@@ -200,6 +201,17 @@ __device__ __forceinline__ void stage_tile_twiddles(const ColParams &p, float2 *
     }
 }
 
+// f(std::integral_constant<int, U>) for every U of the sequence, or for the
+// U below n.
+template <typename F, int... U>
+__device__ __forceinline__ void for_slots(F &&f, std::integer_sequence<int, U...>) {
+    (f(std::integral_constant<int, U>{}), ...);
+}
+template <typename F, int... U>
+__device__ __forceinline__ void for_slots_below(F &&f, int n, std::integer_sequence<int, U...>) {
+    ((U < n ? f(std::integral_constant<int, U>{}) : void()), ...);
+}
+
 // Widest column butterfly kernel A may use next to its register window.
 // Window registers per thread are ppt * pt * (2 npol + 1); an r-point
 // butterfly holds r * 2 npol more floats.
@@ -298,51 +310,54 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
             __syncthreads();  // this batch's frames are visible; the other buffer is free
             if (s_base + PT < s_end) stage(s_base + PT, buf ^ 1);
         }
+        // the FIR of one spectrum of the batch (slot u of the window rotation)
+        auto fir_one = [&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            const long long fnew = p.s0 + s_base + u + p.P - 1;  // newest frame of spectrum s_base + u
+            constexpr int snew = (u + PT - 1) % PT;
 #pragma unroll
-        for (int u = 0; u < PT; u++) {
-            if (u < nb) {
-                const long long fnew = p.s0 + s_base + u + p.P - 1;  // newest frame of spectrum s_base + u
-                const int snew = (u + PT - 1) % PT;
+            for (int i = 0; i < PPT; i++) {
+                uint32_t wx;
+                if constexpr (kStaged) {
+                    const unsigned char *rs = raw + ((size_t)(buf * PT + u) * pts + sm_pt[i]) * B;
+                    if constexpr (NPOL == 2) wx = *reinterpret_cast<const uint32_t *>(rs);
+                    else wx = *reinterpret_cast<const unsigned short *>(rs);
+                } else {
+                    wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]);
+                }
+                wx ^= 0x80808080u;
+                T *d = data + u * pts + sm_pt[i];
+                if constexpr (kPacked) {
+                    win2[i][snew] = unpack_p2(wx);
+                    const P2 &w0 = win2[i][u % PT];
+                    P2 y{__fmul2_rn(cf2[i][0], w0.re), __fmul2_rn(cf2[i][0], w0.im)};
 #pragma unroll
-                for (int i = 0; i < PPT; i++) {
-                    uint32_t wx;
-                    if constexpr (kStaged) {
-                        const unsigned char *rs = raw + ((size_t)(buf * PT + u) * pts + sm_pt[i]) * B;
-                        if constexpr (NPOL == 2) wx = *reinterpret_cast<const uint32_t *>(rs);
-                        else wx = *reinterpret_cast<const unsigned short *>(rs);
-                    } else {
-                        wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]);
+                    for (int t = 1; t < PT; t++) {
+                        const P2 &wt = win2[i][(u + t) % PT];
+                        y.re = __ffma2_rn(cf2[i][t], wt.re, y.re);
+                        y.im = __ffma2_rn(cf2[i][t], wt.im, y.im);
                     }
-                    wx ^= 0x80808080u;
-                    T *d = data + u * pts + sm_pt[i];
-                    if constexpr (kPacked) {
-                        win2[i][snew] = unpack_p2(wx);
-                        const P2 &w0 = win2[i][u % PT];
-                        P2 y{__fmul2_rn(cf2[i][0], w0.re), __fmul2_rn(cf2[i][0], w0.im)};
+                    *d = y;
+                } else {
 #pragma unroll
-                        for (int t = 1; t < PT; t++) {
-                            const P2 &wt = win2[i][(u + t) % PT];
-                            y.re = __ffma2_rn(cf2[i][t], wt.re, y.re);
-                            y.im = __ffma2_rn(cf2[i][t], wt.im, y.im);
-                        }
-                        *d = y;
-                    } else {
+                    for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
+                    float y[NC];
 #pragma unroll
-                        for (int k = 0; k < NC; k++) win[i][snew][k] = unpack_byte(wx, k);
-                        float y[NC];
+                    for (int k = 0; k < NC; k++) y[k] = cf[i][0] * win[i][u % PT][k];
 #pragma unroll
-                        for (int k = 0; k < NC; k++) y[k] = cf[i][0] * win[i][u % PT][k];
+                    for (int t = 1; t < PT; t++) {
 #pragma unroll
-                        for (int t = 1; t < PT; t++) {
-#pragma unroll
-                            for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
-                        }
-                        if constexpr (NPOL == 2) *d = make_p2(y[0], y[1], y[2], y[3]);
-                        else *d = make_float2(y[0], y[1]);
+                        for (int k = 0; k < NC; k++) y[k] = fmaf(cf[i][t], win[i][(u + t) % PT][k], y[k]);
                     }
+                    if constexpr (NPOL == 2) *d = make_p2(y[0], y[1], y[2], y[3]);
+                    else *d = make_float2(y[0], y[1]);
                 }
             }
-        }
+        };
+        // a full batch has no per-spectrum guards, so the PT spectra's
+        // independent FMA chains interleave freely
+        if (nb == PT) for_slots(fir_one, std::make_integer_sequence<int, PT>{});
+        else for_slots_below(fir_one, nb, std::make_integer_sequence<int, PT>{});
         __syncthreads();
         col_fft_store<NPOL, col_radix_cap(NPOL, PT, PPT)>(p, data, x, s_base, nb, tws);
     }
