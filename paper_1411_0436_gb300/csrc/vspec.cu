@@ -585,9 +585,9 @@ vspec_status build_plan(vspec_plan *p) {
 
     const size_t elem = p->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
-    // data [PT][N2][C], twiddle tile [N2][C], PFB: two batches of raw frames
+    // data [PT][N2][C], twiddle tile [N2][C], two batches of raw frames
     p->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2) +
-               (PT > 1 && !p->gather ? 2 * (size_t)PT * N2 * C * p->npol * 2 : 0);
+               (!p->gather ? 2 * (size_t)PT * N2 * C * p->npol * 2 : 0);
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
     if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);
@@ -1387,7 +1387,7 @@ vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
     const size_t elem = c->npol == 2 ? sizeof(float4) : sizeof(float2);
     const size_t accel = c->npol == 2 ? sizeof(float4) : sizeof(float);
     c->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2) +
-               (PT > 1 ? 2 * (size_t)PT * N2 * C * c->npol * 2 : 0);  // + twiddle tile, raw frames
+               2 * (size_t)PT * N2 * C * c->npol * 2;  // + twiddle tile, raw frames
     c->smemB = (size_t)c->RB * (N1 + (N1 >> 4)) * elem + (size_t)c->RB * N1 * accel;
     VSPEC_CUDA(raise_smem_cap(c->kA, c->smemA));
     VSPEC_CUDA(raise_smem_cap(c->kB, c->smemB));

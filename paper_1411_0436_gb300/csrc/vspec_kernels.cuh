@@ -279,10 +279,10 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
         }
     }
 
-    // PFB: each batch's PT new frames are copied into shared memory with
+    // each batch's PT new frames are copied into shared memory with
     // asynchronous copies one batch ahead (double-buffered), so the FIR reads
     // them without waiting on HBM
-    constexpr bool kStaged = PT > 1;
+    constexpr bool kStaged = true;
     constexpr int B = 2 * NPOL;  // bytes per sample
     unsigned char *raw = reinterpret_cast<unsigned char *>(const_cast<float2 *>(tws) + pts);  // [2][PT][pts]
     auto stage = [&](int sb, int buf) {
