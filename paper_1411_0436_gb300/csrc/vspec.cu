@@ -166,6 +166,8 @@ struct vspec_plan {
     // host-input pipeline (vspec_execute_host), created on first use
     bool host_ready = false;
     int host_mode = VSPEC_HOST_STAGED;
+    size_t host_chunk_bytes = 32u << 20;
+    size_t host_bytes = 0;  // device memory of the host pipeline
     cudaStream_t copy_st = nullptr, comp_st = nullptr;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
@@ -317,6 +319,26 @@ const void *pick_kernel_fused(int logn1, int pt) {
     return nullptr;
 }
 
+// Streams, events and staging buffers of vspec_execute_host.
+void release_host_pipeline(vspec_plan *p) {
+    if (!p->host_ready) return;
+    cudaStreamDestroy(p->copy_st);
+    cudaStreamDestroy(p->comp_st);
+    cudaEventDestroy(p->ev_start);
+    cudaEventDestroy(p->ev_done);
+    for (int b = 0; b < 2; b++) {
+        cudaEventDestroy(p->ev_copied[b]);
+        cudaEventDestroy(p->ev_used[b]);
+        cudaFree(p->stage[b]);
+        p->stage[b] = nullptr;
+    }
+    cudaFree(p->hacc);
+    p->hacc = nullptr;
+    p->scratch_bytes -= p->host_bytes;
+    p->host_bytes = 0;
+    p->host_ready = false;
+}
+
 void free_plan(vspec_plan *p) {
     if (!p) return;
     release_records(p);
@@ -328,18 +350,7 @@ void free_plan(vspec_plan *p) {
         cudaEventDestroy(p->ev_assist);
     }
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
-    if (p->host_ready) {
-        cudaStreamDestroy(p->copy_st);
-        cudaStreamDestroy(p->comp_st);
-        cudaEventDestroy(p->ev_start);
-        cudaEventDestroy(p->ev_done);
-        for (int b = 0; b < 2; b++) {
-            cudaEventDestroy(p->ev_copied[b]);
-            cudaEventDestroy(p->ev_used[b]);
-            cudaFree(p->stage[b]);
-        }
-        cudaFree(p->hacc);
-    }
+    release_host_pipeline(p);
     cudaFree(p->coef);
     cudaFree(p->twA);
     cudaFree(p->twB);
@@ -1118,11 +1129,13 @@ vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset, cons
     return VSPEC_OK;
 }
 
-// Spectra per chunk of the host-input pipeline: about 32 MiB of input per
-// staging buffer (at least 16 spectra), so copies and compute overlap.
+// Spectra per chunk of the host-input pipeline: about host_chunk_bytes of
+// input per staging buffer (at least 16 spectra), so copies and compute
+// overlap; the pipeline exposes one chunk's copy at the start and one
+// chunk's compute at the end.
 static int host_chunk_spectra(const vspec_plan *p) {
     const size_t per = (size_t)p->N * p->nsub * p->npol * 2;
-    return (int)std::max<size_t>(16, (32u << 20) / per);
+    return (int)std::max<size_t>(16, p->host_chunk_bytes / per);
 }
 
 vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspectra, float *h_out,
@@ -1150,6 +1163,7 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
             VSPEC_CUDA(cudaEventCreateWithFlags(&p->ev_used[b], cudaEventDisableTiming));
         }
         p->scratch_bytes += tot;
+        p->host_bytes = tot;
         p->host_ready = true;
     }
     // both internal streams start after the work already queued on `stream`
@@ -1202,9 +1216,16 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     return VSPEC_OK;
 }
 
-vspec_status vspec_plan_set_host_mode(vspec_plan *plan, int mode) {
+vspec_status vspec_plan_set_host_mode(vspec_plan *plan, int mode, size_t chunk_bytes) {
     if (!plan || mode < VSPEC_HOST_AUTO || mode > VSPEC_HOST_MAPPED) return VSPEC_ERR_INVALID_ARG;
+    if (chunk_bytes != 0 && (chunk_bytes < (1u << 20) || chunk_bytes > (1ull << 32))) return VSPEC_ERR_INVALID_ARG;
+    const size_t bytes = chunk_bytes ? chunk_bytes : (size_t)(32u << 20);
+    if (plan->host_ready && bytes != plan->host_chunk_bytes) {  // staging buffers are sized by the chunk
+        VSPEC_CUDA(cudaDeviceSynchronize());
+        release_host_pipeline(plan);
+    }
     plan->host_mode = mode;
+    plan->host_chunk_bytes = bytes;
     return VSPEC_OK;
 }
 

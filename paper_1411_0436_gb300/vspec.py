@@ -114,7 +114,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_get_tuning.restype = i
         lib.vspec_plan_set_tuning.argtypes = [vp, ctypes.POINTER(VspecTuning)]
         lib.vspec_plan_set_tuning.restype = i
-        lib.vspec_plan_set_host_mode.argtypes = [vp, i]
+        lib.vspec_plan_set_host_mode.argtypes = [vp, i, ctypes.c_size_t]
         lib.vspec_plan_set_host_mode.restype = i
         lib.vspec_status_string.argtypes = [i]
         lib.vspec_status_string.restype = cp
@@ -257,8 +257,8 @@ def vspec_plan_set_tuning(plan: int, chunk_spectra: int, blocks_a: int, blocks_b
 HOST_AUTO, HOST_STAGED, HOST_MAPPED = 0, 1, 2
 
 
-def vspec_plan_set_host_mode(plan: int, mode: int) -> None:
-    st = load().vspec_plan_set_host_mode(plan, mode)
+def vspec_plan_set_host_mode(plan: int, mode: int, chunk_bytes: int = 0) -> None:
+    st = load().vspec_plan_set_host_mode(plan, mode, chunk_bytes)
     if st != OK:
         raise VspecError(st, "vspec_plan_set_host_mode")
 
@@ -317,8 +317,8 @@ class Plan:
         """Host input -> host output with overlapped copies (see vspec_execute_host)."""
         vspec_execute_host(self.handle, h_in, nspectra, h_out, stream)
 
-    def set_host_mode(self, mode: int) -> None:
-        vspec_plan_set_host_mode(self.handle, mode)
+    def set_host_mode(self, mode: int, chunk_bytes: int = 0) -> None:
+        vspec_plan_set_host_mode(self.handle, mode, chunk_bytes)
 
     def dump(self, d_accum, h_out=None, stream=None) -> None:
         vspec_dump(self.handle, d_accum, h_out, stream)

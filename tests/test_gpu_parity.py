@@ -213,9 +213,10 @@ def test_execute_host_pipeline_matches_oracle(oracle_mod, cfg):
     pageable = np.ascontiguousarray(x.view(np.uint8).reshape(-1))
     with Plan(n, p, npol, mode, win) as plan:
         h_out = torch.empty(plan.out_floats, dtype=torch.float32).pin_memory()
-        for host_mode, h_in in ((HOST_STAGED, pinned), (HOST_MAPPED, pinned), (HOST_AUTO, pinned),
-                                (HOST_AUTO, pageable)):
-            plan.set_host_mode(host_mode)
+        for host_mode, h_in, chunk in ((HOST_STAGED, pinned, 0), (HOST_STAGED, pinned, 1 << 20),
+                                       (HOST_MAPPED, pinned, 0), (HOST_AUTO, pinned, 0),
+                                       (HOST_AUTO, pageable, 0)):
+            plan.set_host_mode(host_mode, chunk)
             for _ in range(2):
                 h_out.fill_(123.0)
                 plan.execute_host(h_in, s, h_out)
@@ -235,6 +236,8 @@ def test_mapped_host_mode_rejects_pageable_input():
         assert e.value.status == vspec.ERR_INVALID_ARG
         with pytest.raises(vspec.VspecError):
             plan.set_host_mode(3)
+        with pytest.raises(vspec.VspecError):
+            plan.set_host_mode(vspec.HOST_STAGED, 1000)  # below 1 MiB
 
 
 def test_batch_graph_matches_single_banks(oracle_mod):
