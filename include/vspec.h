@@ -88,7 +88,7 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
 #define VSPEC_PLAN_TENSOR 2u     /* two-kernel path with the first radix-16 pass of every
                                     2048-point row on the tensor cores (bf16 hi/lo operands,
                                     fp32 accumulation, see vspec_tc_dft16); dual-pol only,
-                                    nchan 2^11..2^19 where the rows are 2048 points; other
+                                    nchan 2^11..2^20 where the rows are 2048 points; other
                                     sizes return VSPEC_ERR_UNSUPPORTED */
 #define VSPEC_PLAN_KAHAN 4u      /* compensated (Kahan) FP32 accumulation at every level: over
                                     spectra in the kernel, across groups and into the caller's

@@ -498,7 +498,7 @@ vspec_status build_plan(vspec_plan *p) {
         N <= 32768 && (!pfb || p->P == 8))
         return build_fused_plan(p);
     int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
-    int cmin = p->npol == 2 ? 16 : 32;  // 64-byte row segments of int8 input
+    int cmin = 32 / (2 * p->npol);  // 32-byte row segments of int8 input (one sector)
     // largest column length kernel A can hold in registers (512 threads, at
     // most 4096 points, the FIR window's registers allowing)
     auto n2max = [&]() { return PT == 1 ? 4096 / cmin : PT <= 8 ? 1024 / cmin : 512 / cmin; };
@@ -513,11 +513,6 @@ vspec_status build_plan(vspec_plan *p) {
     p->gather = pfb && N / N2 > 4096;
     if (p->gather) {
         PT = 1;
-        grow();
-    }
-    // single-pol at the largest sizes: 32-byte row segments, longer columns
-    if (N / N2 > 4096 && cmin == 32) {
-        cmin = 16;
         grow();
     }
     const int N1 = N / N2;
@@ -575,7 +570,7 @@ vspec_status build_plan(vspec_plan *p) {
     p->TB = std::min(256, std::max(32, maxb));
     if (p->flags & VSPEC_PLAN_TENSOR) {
         if (p->npol != 2 || N1 != vspec::kTcN1 || p->RB != 1 || p->passB[0].r != 16) {
-            g_last_error = "tensor-core stage needs dual-pol and 2048-point rows (nchan 2^11 .. 2^19)";
+            g_last_error = "tensor-core stage needs dual-pol and 2048-point rows (nchan 2^11 .. 2^20)";
             return VSPEC_ERR_UNSUPPORTED;
         }
         p->tc = true;

@@ -333,7 +333,7 @@ def test_tensor_core_plan_matches_oracle(oracle_mod, cfg):
 
 def test_tensor_core_plan_rejects_other_sizes():
     from paper_1411_0436_gb300 import vspec
-    for args in [(1024, 8, 2, PFB, WIN_HANN), (262144, 8, 2, PFB, WIN_HANN), (32768, 8, 1, PFB, WIN_HANN)]:
+    for args in [(1024, 8, 2, PFB, WIN_HANN), (512, 1, 2, DIRECT, WIN_RECT), (32768, 8, 1, PFB, WIN_HANN)]:
         with pytest.raises(vspec.VspecError) as e:
             vspec.Plan(*args, flags=vspec.PLAN_TENSOR)
         assert e.value.status == vspec.ERR_UNSUPPORTED
