@@ -725,8 +725,8 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
 // 0.62 of it with an 8-tap PFB, 0.70 in direct mode). With only a few idle
 // SMs the second path's fixed cost outweighs them.
 constexpr int kTwoKernelFrom[2][5] = {
-    {INT_MAX, 750, 470, 120, 0},   // PFB, nchan 2048 .. 32768
-    {INT_MAX, 2090, 720, 210, 40}  // direct
+    {INT_MAX, 900, 300, 100, 0},   // PFB, nchan 2048 .. 32768
+    {INT_MAX, 1500, 400, 130, 90}  // direct
 };
 constexpr double kAssistPerSmRate = 0.62;        // PFB
 constexpr double kAssistPerSmRateDirect = 0.70;  // direct FFT
