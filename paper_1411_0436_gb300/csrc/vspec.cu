@@ -714,9 +714,9 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
 // (1) Long calls: the two-kernel path spreads its work evenly over every SM
 // and hides its memory latency better, and beyond a per-size number of
 // spectra it is the faster path; below it the fused kernel's smaller fixed
-// cost wins. The thresholds come from measurements on GB300 (time = fixed +
-// per-spectrum cost for both paths, 100 to 4000 spectra); at 2048 channels
-// the fused path is faster at every length.
+// cost wins. The thresholds come from measurements on GB300 (both paths
+// timed at 50 to 4000 spectra per call); at 2048 channels the fused path is
+// faster at every length.
 // (2) Assist: on a device whose SM count is not a multiple of the cluster
 // size, the two-kernel plan can channelize a share of a call's spectra on
 // the SMs the clusters leave idle, concurrently with the fused kernel. The
