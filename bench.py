@@ -551,6 +551,7 @@ def run_batch(args):
     ns = [b.nspectra for b in banks]
     stream = torch.cuda.current_stream(dev)
     flags = batch.autotune(d_in, ns, accs, stream, reps=3)
+    batch_shapes = [batch.bank_tuning(i)[1] for i in range(len(flags))]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -579,6 +580,7 @@ def run_batch(args):
         "config": {"workload": "8 dual-pol banks 1024..524288 channels, PFB-8/direct alternating, "
                                "2048..64 spectra, one CUDA-graph launch per step",
                    "input_bytes": int(in_bytes), "bank_flags": flags,
+                   "bank_shapes": [batch_shapes[i] for i in range(len(flags))],
                    "l2": "flushed between steps (256 MiB write outside the timed interval)"},
         "path_roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                           "peak_source": peak_kind},

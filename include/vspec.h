@@ -360,16 +360,22 @@ VSPEC_API vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *con
                                            const int *nspectra, float *const *d_accum, void *stream);
 
 /*
- * Autotuner: for each bank, time `reps` executions of every applicable kernel
- * path (the one-pass fused path and the two-kernel path) on the given
- * arguments and keep the faster plan. Clears every d_accum[i] afterwards and
- * synchronises `stream`. vspec_batch_bank_flags reports the VSPEC_PLAN_*
- * flags of the plan chosen for bank `bank`.
+ * Autotuner: for each bank, time `reps` executions (after one warm-up) of
+ * every candidate on the given arguments and keep the fastest: the default
+ * plan and the two-kernel plan (VSPEC_PLAN_TWO_KERNEL), each in several launch
+ * shapes (vspec_plan_set_tuning): its default, a chunk half as long, kernel B
+ * over two waves of CTAs, and for a plan that can switch between the fused
+ * and the two-kernel path, each path alone. Clears every d_accum[i]
+ * afterwards and synchronises `stream`. vspec_batch_bank_flags reports the
+ * VSPEC_PLAN_* flags of the plan chosen for bank `bank`;
+ * vspec_batch_bank_tuning also its launch shape (either pointer may be NULL).
  */
 VSPEC_API vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
                                             const int *nspectra, float *const *d_accum,
                                             void *stream, int reps);
 VSPEC_API vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags);
+VSPEC_API vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigned *flags,
+                                               vspec_tuning *tuning);
 
 /*
  * Batched 16-point DFTs on the tensor cores (tcgen05.mma, bf16 operands,

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -20,6 +21,7 @@ struct vspec_batch {
     std::vector<vspec_bank> desc;
     std::vector<vspec_plan *> plans;
     std::vector<unsigned> flags;
+    std::vector<vspec_tuning> tuning;  // launch shape the autotuner chose
     std::vector<cudaStream_t> branch;
     std::vector<cudaEvent_t> joined;
     cudaStream_t capture = nullptr;
@@ -109,6 +111,7 @@ vspec_status vspec_batch_create(vspec_batch **out, int nbanks, const vspec_bank 
     b->nbanks = nbanks;
     b->desc.assign(banks, banks + nbanks);
     b->flags.assign(nbanks, 0u);
+    b->tuning.assign(nbanks, vspec_tuning{});
     for (int i = 0; i < nbanks; i++) {
         vspec_plan *p = nullptr;
         const vspec_bank &d = banks[i];
@@ -164,40 +167,77 @@ vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) return VSPEC_ERR_CUDA;
     vspec_status result = VSPEC_OK;
+    // time one plan in its current shape: a warm-up execute, then reps
+    auto time_plan = [&](vspec_plan *p, int i, float *ms) -> bool {
+        vspec_status s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);
+        cudaEventRecord(t0, st);
+        for (int r = 0; r < reps && s == VSPEC_OK; r++) s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);
+        cudaEventRecord(t1, st);
+        return s == VSPEC_OK && cudaEventSynchronize(t1) == cudaSuccess &&
+               cudaEventElapsedTime(ms, t0, t1) == cudaSuccess;
+    };
     for (int i = 0; i < batch->nbanks && result == VSPEC_OK; i++) {
         const vspec_bank &d = batch->desc[i];
         const unsigned cand[2] = {0u, VSPEC_PLAN_TWO_KERNEL};
         float best = 1e30f;
         vspec_plan *best_plan = nullptr;
         unsigned best_flags = 0;
+        vspec_tuning best_tuning{};
         for (unsigned f : cand) {
             vspec_plan *p = nullptr;
             if (vspec_plan_create_ex(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window, f) != VSPEC_OK) continue;
-            vspec_status s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);  // warm-up
-            cudaEventRecord(t0, st);
-            for (int r = 0; r < reps && s == VSPEC_OK; r++)
-                s = vspec_execute(p, d_in[i], nspectra[i], d_accum[i], stream);
-            cudaEventRecord(t1, st);
-            float ms = 0.f;
-            if (s == VSPEC_OK && cudaEventSynchronize(t1) == cudaSuccess &&
-                cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best) {
-                if (best_plan) vspec_plan_destroy(best_plan);
-                best_plan = p;
-                best = ms;
-                best_flags = f;
-            } else {
-                cudaStreamSynchronize(st);
-                vspec_plan_destroy(p);
+            // launch shapes: the plan's default, a chunk half as long, kernel B
+            // over two waves of CTAs, and for a fused plan each path alone
+            vspec_tuning def{}, lim{};
+            vspec_plan_get_tuning(p, &def, &lim);
+            std::vector<vspec_tuning> shapes{def};
+            if (def.chunk_spectra > 1) {
+                vspec_tuning t = def;
+                t.chunk_spectra = def.chunk_spectra / 2;
+                shapes.push_back(t);
             }
+            if (def.chunk_spectra > 0 && lim.blocks_b >= 2) {
+                vspec_tuning t = def;
+                t.blocks_b = lim.blocks_b / 2;  // the limit is four waves
+                shapes.push_back(t);
+            }
+            if (lim.two_kernel_from > 0) {  // a fused plan owning a two-kernel plan
+                for (int from : {0, INT_MAX}) {
+                    if (from == def.two_kernel_from) continue;
+                    vspec_tuning t = def;
+                    t.two_kernel_from = from;
+                    shapes.push_back(t);
+                }
+            }
+            bool kept = false;
+            for (const vspec_tuning &t : shapes) {
+                float ms = 0.f;
+                if (vspec_plan_set_tuning(p, &t) != VSPEC_OK || !time_plan(p, i, &ms)) {
+                    cudaStreamSynchronize(st);
+                    continue;
+                }
+                if (ms < best) {
+                    if (best_plan && best_plan != p) vspec_plan_destroy(best_plan);
+                    best_plan = p;
+                    best = ms;
+                    best_flags = f;
+                    best_tuning = t;
+                    kept = true;
+                }
+            }
+            cudaStreamSynchronize(st);
+            if (!kept) vspec_plan_destroy(p);
         }
         if (!best_plan) {
             result = VSPEC_ERR_CUDA;
             break;
         }
         cudaStreamSynchronize(st);
+        if (vspec_plan_set_tuning(best_plan, &best_tuning) != VSPEC_OK) result = VSPEC_ERR_CUDA;
         vspec_plan_destroy(batch->plans[i]);
         batch->plans[i] = best_plan;
         batch->flags[i] = best_flags;
+        batch->tuning[i] = best_tuning;
         const size_t bytes = (size_t)d.nchan * (d.npol == 2 ? 4 : 1) * sizeof(float);
         if (cudaMemsetAsync(d_accum[i], 0, bytes, st) != cudaSuccess) result = VSPEC_ERR_CUDA;
     }
@@ -208,6 +248,13 @@ vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     return result;
+}
+
+vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigned *flags, vspec_tuning *tuning) {
+    if (!batch || bank < 0 || bank >= batch->nbanks) return VSPEC_ERR_INVALID_ARG;
+    if (flags) *flags = batch->flags[bank];
+    if (tuning) return vspec_plan_get_tuning(batch->plans[bank], tuning, nullptr);
+    return VSPEC_OK;
 }
 
 vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags) {

@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_autotune.restype = i
         lib.vspec_batch_bank_flags.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint)]
         lib.vspec_batch_bank_flags.restype = i
+        lib.vspec_batch_bank_tuning.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(VspecTuning)]
+        lib.vspec_batch_bank_tuning.restype = i
         lib.vspec_plan_check.argtypes = [vp]
         lib.vspec_plan_check.restype = i
         lib.vspec_tc_dft16.argtypes = [vp, vp, i, i, vp]
@@ -426,6 +428,14 @@ class Batch:
             load().vspec_batch_bank_flags(self.handle, i, ctypes.byref(f))
             out.append(int(f.value))
         return out
+
+    def bank_tuning(self, i: int):
+        """(flags, launch shape as a dict) of the plan bank i runs."""
+        f, t = ctypes.c_uint(), VspecTuning()
+        st = load().vspec_batch_bank_tuning(self.handle, i, ctypes.byref(f), ctypes.byref(t))
+        if st != OK:
+            raise VspecError(st, "vspec_batch_bank_tuning")
+        return int(f.value), {k: int(getattr(t, k)) for k, _ in VspecTuning._fields_}
 
     def close(self) -> None:
         if self.handle:

@@ -255,6 +255,9 @@ def test_batch_graph_matches_single_banks(oracle_mod):
         ns = [b.nspectra for b in banks]
         flags = batch.autotune(d_in, ns, accs, reps=2)
         assert len(flags) == len(banks)
+        for i, f in enumerate(flags):  # the chosen plan form and launch shape are reported
+            f2, shape = batch.bank_tuning(i)
+            assert f2 == f and shape["blocks_a"] >= 0 and shape["blocks_b"] >= 0
         for rep in range(3):   # capture, replay, replay
             for a in accs:
                 a.zero_()
