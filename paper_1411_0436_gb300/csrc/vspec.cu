@@ -205,6 +205,18 @@ template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
     return nullptr;
 }
 
+// register-column kernel A (dual-pol PFB, 8 taps, 512-point tiles) for N2 in 2 .. 16
+const void *pick_kernel_colreg(int N2, size_t *smem) {
+    using namespace vspec;
+    switch (N2) {
+        case 2: *smem = ColReg<2>::smem; return (const void *)fir_colreg_kernel<2>;
+        case 4: *smem = ColReg<4>::smem; return (const void *)fir_colreg_kernel<4>;
+        case 8: *smem = ColReg<8>::smem; return (const void *)fir_colreg_kernel<8>;
+        case 16: *smem = ColReg<16>::smem; return (const void *)fir_colreg_kernel<16>;
+    }
+    return nullptr;
+}
+
 constexpr int kNumKinds = 4;
 const char *const kKindNames[kNumKinds] = {"fir_colfft", "rowfft_detect", "reduce", "fused_channelize"};
 
@@ -555,7 +567,14 @@ vspec_status build_plan(vspec_plan *p) {
     // the butterfly width so both fit in 128 registers.
     const int capA = vspec::col_radix_cap(p->npol, PT, PPT);
     const int maxbitsA = capA == 16 ? 4 : capA == 8 ? 3 : 2;
-    const std::vector<int> rA = radix_list(e2, maxbitsA), rB = radix_list(e1);
+    // dual-pol PFB (5 .. 8 taps) with columns of 2 .. 16 points in 512-point
+    // tiles: the register-column kernel A, whose column DFT is one radix-N2
+    // pass (natural output order)
+    size_t smem_colreg = 0;
+    const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512
+                             ? pick_kernel_colreg(N2, &smem_colreg) : nullptr;
+    if (colreg) p->kernelA = colreg;
+    const std::vector<int> rA = colreg ? std::vector<int>{N2} : radix_list(e2, maxbitsA), rB = radix_list(e1);
     int twA_n = 0, twB_n = 0;
     p->passA = make_passes(N2, rA, &twA_n);
     p->passB = make_passes(N1, rB, &twB_n);
@@ -594,6 +613,7 @@ vspec_status build_plan(vspec_plan *p) {
     // data [PT][N2][C], twiddle tile [N2][C], two batches of raw frames
     p->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2) +
                (!p->gather ? 2 * (size_t)PT * N2 * C * p->npol * 2 : 0);
+    if (colreg) p->smemA = smem_colreg;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
     if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);

@@ -383,6 +383,125 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     }
 }
 
+// Kernel A, register-column form: dual-pol PFB of at most 8 taps whose
+// columns are at most 16 points (nchan 2^12 .. 2^15 with 2048-point rows).
+// The FIR stage is the same register window as above (one point per thread,
+// 512 points per tile); the column DFTs are then whole length-N2 transforms
+// in registers, one column per thread, instead of radix passes through
+// shared memory. Outputs come out in natural order (the plan's column pass
+// list is the single radix-N2 pass, so pos = k2), each multiplied by
+// W_N^(n1 k2) on its way to the chunk scratch. SPB spectra share a column
+// pass so that all 512 threads hold a column: SPB * C = 512 * CPT.
+template <int N2>
+struct ColReg {
+    static constexpr int PT = 8, PTS = 512, C = PTS / N2;
+    static constexpr int SPB = N2 > PT ? N2 : PT;
+    static constexpr int CPT = SPB * C / PTS;  // columns per thread per pass
+    // data [SPB][PTS] P2, twiddle tile [N2][C] float2, raw frames [2][SPB][PTS]
+    // u32, coefficients [PT][PTS] float
+    static constexpr size_t smem =
+        (size_t)SPB * PTS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 + (size_t)PT * PTS * 4;
+};
+
+template <int N2>
+__global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__ ColParams p) {
+    using G = ColReg<N2>;
+    constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB, CPT = G::CPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][PTS]
+    float2 *tws = reinterpret_cast<float2 *>(data + SPB * PTS);        // [N2][C]
+    uint32_t *raw = reinterpret_cast<uint32_t *>(tws + PTS);           // [2][SPB][PTS]
+    float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);       // [PT][PTS]
+    const int t = threadIdx.x;                                         // point n2 * C + c
+    const int D = PT - p.P;                                            // leading zero taps
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        const int n1_0 = x * C;
+        for (int e = t; e < PTS; e += blockDim.x)  // W_N^(n1 k2), k2 = pos
+            tws[e] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
+
+        const long long n_pt = n1_0 + (t % C) + (long long)p.N1 * (t / C);
+        // the tile's coefficients, read back for every batch so that their
+        // registers are free during the column DFTs (each thread reads only
+        // what it wrote: no barrier needed)
+#pragma unroll
+        for (int k = 0; k < PT; k++) cfs[k * PTS + t] = k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) : 0.f;
+        // slot (s - s_beg + k) % PT of the window holds frame s + k - D
+        P2 win[PT];
+        const long long sabs = p.s0 + s_beg;
+#pragma unroll
+        for (int k = 0; k < PT - 1; k++) {
+            long long fr = sabs - D + k;
+            if (fr < 0) fr = 0;
+            win[k] = unpack_p2(load_raw<2>(p.in, fr * p.N + n_pt) ^ 0x80808080u);
+        }
+        // the newest frames of SPB spectra, one batch ahead, 16-byte copies
+        auto stage = [&](int sb, int buf) {
+            const int nbb = min(SPB, s_end - sb);
+            constexpr int per_row = C / 4, per_frame = PTS / 4;
+            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
+                const int u = e / per_frame, r = e % per_frame;
+                const int n2 = r / per_row, ch = r % per_row;
+                const long long fr = p.s0 + sb + u + p.P - 1;
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
+                                      (long long)p.N1 * n2 + ch * 4;
+                uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        stage(s_beg, 0);
+        for (int s_base = s_beg, buf = 0; s_base < s_end; s_base += SPB, buf ^= 1) {
+            const int nb = min(SPB, s_end - s_base);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // frames visible; the other buffer and data are free
+            if (s_base + SPB < s_end) stage(s_base + SPB, buf ^ 1);
+            float2 cf2[PT];
+#pragma unroll
+            for (int k = 0; k < PT; k++) cf2[k] = dup2(cfs[k * PTS + t]);
+            auto fir_one = [&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                constexpr int snew = (u + PT - 1) % PT;
+                win[snew] = unpack_p2(raw[(buf * SPB + u) * PTS + t] ^ 0x80808080u);
+                const P2 &w0 = win[u % PT];
+                P2 y{__fmul2_rn(cf2[0], w0.re), __fmul2_rn(cf2[0], w0.im)};
+#pragma unroll
+                for (int k = 1; k < PT; k++) {
+                    const P2 &wk = win[(u + k) % PT];
+                    y.re = __ffma2_rn(cf2[k], wk.re, y.re);
+                    y.im = __ffma2_rn(cf2[k], wk.im, y.im);
+                }
+                data[u * PTS + t] = y;
+            };
+            if (nb == SPB) for_slots(fir_one, std::make_integer_sequence<int, SPB>{});
+            else for_slots_below(fir_one, nb, std::make_integer_sequence<int, SPB>{});
+            __syncthreads();  // the batch's pre-filter outputs are in data
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+                const int col = t + k * PTS;  // = sb * C + c
+                const int sb = col / C, c = col % C;
+                if (sb < nb) {
+                    P2 v[N2];
+#pragma unroll
+                    for (int q = 0; q < N2; q++) v[q] = data[sb * PTS + q * C + c];
+                    Dft<N2>::run(v);
+                    P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                    z[0] = v[0];
+#pragma unroll
+                    for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
+                }
+            }
+        }
+        __syncthreads();  // the column passes are done with the twiddle tile
+    }
+}
+
 // Kernel A for transforms too long for a register FIR window next to the
 // column tile (PFB with nchan above 2^18): every spectrum's P taps are read
 // straight from the input (the P frames a spectrum spans stay in L2 while
