@@ -205,14 +205,18 @@ template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
     return nullptr;
 }
 
-// register-column kernel A (dual-pol PFB, 8 taps, 512-point tiles) for N2 in 2 .. 16
-const void *pick_kernel_colreg(int N2, size_t *smem) {
+// register-column kernel A (dual-pol PFB, 8 taps, 512-point tiles) for N2 in
+// 2 .. 64 and its column pass list (one pass up to 16 points, then 8 x N2/8)
+const void *pick_kernel_colreg(int N2, size_t *smem, std::vector<int> *radices) {
     using namespace vspec;
+    *radices = N2 <= 16 ? std::vector<int>{N2} : std::vector<int>{8, N2 / 8};
     switch (N2) {
         case 2: *smem = ColReg<2>::smem; return (const void *)fir_colreg_kernel<2>;
         case 4: *smem = ColReg<4>::smem; return (const void *)fir_colreg_kernel<4>;
         case 8: *smem = ColReg<8>::smem; return (const void *)fir_colreg_kernel<8>;
         case 16: *smem = ColReg<16>::smem; return (const void *)fir_colreg_kernel<16>;
+        case 32: *smem = ColReg<32, 8>::smem; return (const void *)fir_colreg_kernel<32, 8>;
+        case 64: *smem = ColReg<64, 8>::smem; return (const void *)fir_colreg_kernel<64, 8>;
     }
     return nullptr;
 }
@@ -567,14 +571,14 @@ vspec_status build_plan(vspec_plan *p) {
     // the butterfly width so both fit in 128 registers.
     const int capA = vspec::col_radix_cap(p->npol, PT, PPT);
     const int maxbitsA = capA == 16 ? 4 : capA == 8 ? 3 : 2;
-    // dual-pol PFB (5 .. 8 taps) with columns of 2 .. 16 points in 512-point
-    // tiles: the register-column kernel A, whose column DFT is one radix-N2
-    // pass (natural output order)
+    // dual-pol PFB (5 .. 8 taps) with columns of 2 .. 64 points in 512-point
+    // tiles: the register-column kernel A and its own column pass list
     size_t smem_colreg = 0;
+    std::vector<int> r_colreg;
     const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512
-                             ? pick_kernel_colreg(N2, &smem_colreg) : nullptr;
+                             ? pick_kernel_colreg(N2, &smem_colreg, &r_colreg) : nullptr;
     if (colreg) p->kernelA = colreg;
-    const std::vector<int> rA = colreg ? std::vector<int>{N2} : radix_list(e2, maxbitsA), rB = radix_list(e1);
+    const std::vector<int> rA = colreg ? r_colreg : radix_list(e2, maxbitsA), rB = radix_list(e1);
     int twA_n = 0, twB_n = 0;
     p->passA = make_passes(N2, rA, &twA_n);
     p->passB = make_passes(N1, rB, &twB_n);

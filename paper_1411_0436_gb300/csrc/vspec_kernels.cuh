@@ -383,37 +383,49 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     }
 }
 
-// Kernel A, register-column form: dual-pol PFB of at most 8 taps whose
-// columns are at most 16 points (nchan 2^12 .. 2^15 with 2048-point rows).
-// The FIR stage is the same register window as above (one point per thread,
-// 512 points per tile); the column DFTs are then whole length-N2 transforms
-// in registers, one column per thread, instead of radix passes through
-// shared memory. Outputs come out in natural order (the plan's column pass
-// list is the single radix-N2 pass, so pos = k2), each multiplied by
-// W_N^(n1 k2) on its way to the chunk scratch. SPB spectra share a column
-// pass so that all 512 threads hold a column: SPB * C = 512 * CPT.
-template <int N2>
+// Kernel A, register-column form: dual-pol PFB of at most 8 taps in tiles of
+// 512 points (one per thread) with columns of N2 = 2 .. 64 points (nchan
+// 2^12 .. 2^17 with 2048-point rows). The FIR stage is the same register
+// window as above. Columns of at most 16 points (R1 == N2) are then whole
+// length-N2 DFTs in registers, one column per thread, in natural output
+// order (the plan's column pass list is the single radix-N2 pass, so
+// pos = k2). Longer columns take two DIF passes, radix R1 then N2 / R1, the
+// plan's pass list {R1, N2/R1}, with every index a compile-time function of
+// the thread: the first pass's twiddles come from a small table in shared
+// memory, the second pass writes the chunk scratch. Every output is
+// multiplied by W_N^(n1 k2) on its way out. SPB spectra share a column
+// stage, so that the 512 threads have whole butterflies to work on.
+template <int N2, int R1 = N2>
 struct ColReg {
     static constexpr int PT = 8, PTS = 512, C = PTS / N2;
-    static constexpr int SPB = N2 > PT ? N2 : PT;
-    static constexpr int CPT = SPB * C / PTS;  // columns per thread per pass
+    static constexpr bool kOnePass = R1 == N2;
+    static constexpr int R2 = N2 / R1;  // second-pass radix (two-pass form)
+    static constexpr int SPB = kOnePass && N2 > PT ? N2 : PT;
+    static constexpr int CPT = SPB * C / PTS;             // columns per thread (one pass)
+    static constexpr int B1 = SPB * C * (N2 / R1) / PTS;  // first-pass butterflies per thread
+    static constexpr int B2 = SPB * C * R1 / PTS;         // second-pass butterflies per thread
+    static constexpr int TWC = kOnePass ? 0 : (N2 / R1) * (R1 - 1);  // first-pass twiddles
     // data [SPB][PTS] P2, twiddle tile [N2][C] float2, raw frames [2][SPB][PTS]
-    // u32, coefficients [PT][PTS] float
-    static constexpr size_t smem =
-        (size_t)SPB * PTS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 + (size_t)PT * PTS * 4;
+    // u32, coefficients [PT][PTS] float, first-pass twiddles [TWC] float2
+    static constexpr size_t smem = (size_t)SPB * PTS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 +
+                                   (size_t)PT * PTS * 4 + (size_t)TWC * 8;
+    static_assert(kOnePass ? N2 <= 16 : (R1 == 8 && (N2 == 32 || N2 == 64)), "column shapes of this kernel");
 };
 
-template <int N2>
+template <int N2, int R1 = N2>
 __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__ ColParams p) {
-    using G = ColReg<N2>;
-    constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB, CPT = G::CPT;
+    using G = ColReg<N2, R1>;
+    constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][PTS]
     float2 *tws = reinterpret_cast<float2 *>(data + SPB * PTS);        // [N2][C]
     uint32_t *raw = reinterpret_cast<uint32_t *>(tws + PTS);           // [2][SPB][PTS]
     float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);       // [PT][PTS]
+    float2 *twc = reinterpret_cast<float2 *>(cfs + PT * PTS);          // [N2/R1][R1-1]
     const int t = threadIdx.x;                                         // point n2 * C + c
     const int D = PT - p.P;                                            // leading zero taps
+    // first-pass twiddles W_N2^(j q) (ordered before use by the loop's barriers)
+    for (int e = t; e < G::TWC; e += blockDim.x) twc[e] = __ldg(p.twA + p.pass[0].off + e);
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);
@@ -482,19 +494,58 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
             if (nb == SPB) for_slots(fir_one, std::make_integer_sequence<int, SPB>{});
             else for_slots_below(fir_one, nb, std::make_integer_sequence<int, SPB>{});
             __syncthreads();  // the batch's pre-filter outputs are in data
+            if constexpr (G::kOnePass) {
 #pragma unroll
-            for (int k = 0; k < CPT; k++) {
-                const int col = t + k * PTS;  // = sb * C + c
-                const int sb = col / C, c = col % C;
-                if (sb < nb) {
-                    P2 v[N2];
+                for (int k = 0; k < G::CPT; k++) {
+                    const int col = t + k * PTS;  // = sb * C + c
+                    const int sb = col / C, c = col % C;
+                    if (sb < nb) {
+                        P2 v[N2];
 #pragma unroll
-                    for (int q = 0; q < N2; q++) v[q] = data[sb * PTS + q * C + c];
-                    Dft<N2>::run(v);
-                    P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
-                    z[0] = v[0];
+                        for (int q = 0; q < N2; q++) v[q] = data[sb * PTS + q * C + c];
+                        Dft<N2>::run(v);
+                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        z[0] = v[0];
 #pragma unroll
-                    for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
+                        for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
+                    }
+                }
+            } else {
+                constexpr int M1 = N2 / R1, R2 = G::R2;
+                // first pass: butterfly j of column (sb, c) over positions j + M1 q
+#pragma unroll
+                for (int k = 0; k < G::B1; k++) {
+                    const int e = t + k * PTS;
+                    const int c = e % C, j = (e / C) % M1, sb = e / (C * M1);
+                    if (sb < nb) {
+                        P2 *d = data + sb * PTS + j * C + c;
+                        P2 v[R1];
+#pragma unroll
+                        for (int q = 0; q < R1; q++) v[q] = d[q * M1 * C];
+                        Dft<R1>::run(v);
+                        const float2 *w = twc + j * (R1 - 1);
+                        d[0] = v[0];
+#pragma unroll
+                        for (int q = 1; q < R1; q++) d[q * M1 * C] = cmul(v[q], w[q - 1]);
+                    }
+                }
+                __syncthreads();
+                // second pass: block b of column (sb, c), positions b R2 + q, to the scratch
+#pragma unroll
+                for (int k = 0; k < G::B2; k++) {
+                    const int e = t + k * PTS;
+                    const int c = e % C, b = (e / C) % R1, sb = e / (C * R1);
+                    if (sb < nb) {
+                        const P2 *d = data + sb * PTS + b * R2 * C + c;
+                        P2 v[R2];
+#pragma unroll
+                        for (int q = 0; q < R2; q++) v[q] = d[q * C];
+                        Dft<R2>::run(v);
+                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
+                                (size_t)(b * R2) * p.N1 + n1_0 + c;
+#pragma unroll
+                        for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[(b * R2 + q) * C + c]);
+                    }
                 }
             }
         }
