@@ -116,6 +116,7 @@ std::vector<int> digit_reverse(int L, const std::vector<int> &radices) {
 struct vspec_plan {
     int N = 0, P = 0, npol = 0, mode = 0, window = 0, device = 0;
     int N1 = 0, N2 = 0, C = 0, PT = 0, PPT = 0, TA = 0, RB = 0, TB = 0;
+    int tileG = 1;                   // kernel-A tiles per group (tile_split)
     int num_sms = 0, occA = 1, occB = 1;
     int sc_max = 1;                  // spectra per chunk
     int sc_cap = 1, slots_cap = 1;   // largest chunk a tuning may ask for; slots allocated
@@ -548,6 +549,9 @@ vspec_status build_plan(vspec_plan *p) {
     p->N1 = N1;
     p->N2 = N2;
     p->C = C;
+    // kernel-A blocks in groups that cover 128-byte lines of the input rows
+    // together (a tile row is C samples of npol * 2 bytes)
+    p->tileG = std::max(1, std::min(N1 / C, 128 / (C * p->npol * 2)));
     p->PT = PT;
     p->PPT = PPT;
     p->TA = TA;
@@ -1048,6 +1052,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     ca.npass = (int)p->passA.size();
     for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
     ca.tiles = p->N1 / p->C;
+    ca.G = p->tileG;
 
     vspec::RowParams cb{};
     cb.Z = p->Z;
@@ -1074,8 +1079,9 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
             ca.s0 = s0;
             ca.sc = sc;
             void *argsA[] = {&ca};
-            // no more CTAs than items: every block then has work
-            const int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
+            // no more CTAs than items, and a whole number of tile groups
+            int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
+            ga = std::max(ca.G, ga / ca.G * ca.G);
             vspec_status r = launch(p, 0, sc, p->kernelA, dim3(ga), dim3(p->TA), argsA, p->smemA, st);
             if (r != VSPEC_OK) return r;
         }

@@ -52,6 +52,7 @@ struct ColParams {
     long long s0;        // absolute index of the chunk's first spectrum
     int sc;              // spectra in this chunk
     int tiles;           // column tiles, N1 / C
+    int G;               // tiles per group (tile_split); 0 or 1: no groups
 };
 
 struct RowParams {
@@ -93,6 +94,24 @@ __device__ __forceinline__ int span_slot(int tiles, int sc, int x) {
     const long long T = (long long)tiles * sc;
     const long long k_lo = (((long long)x * sc + 1) * gridDim.x - 1) / T;
     return (int)(blockIdx.x - k_lo);
+}
+
+// Kernel A's split: blocks come in groups of G consecutive blocks that take
+// the same items of the tiles / G super-tiles (block_span over the groups),
+// member r the r-th tile of each super-tile. G adjacent tiles share the
+// input's 128-byte lines (a tile row is C samples), and a group reads them
+// at about the same time, so each line comes from HBM once. Needs G | tiles
+// and G | gridDim.x. Tile of super-tile item f: (f / sc) * G + r.
+struct TileSplit {
+    long long lo, hi;
+    int G, r;
+};
+__device__ __forceinline__ TileSplit tile_split(int tiles, int sc, int G) {
+    if (G < 1) G = 1;
+    const int ng = gridDim.x / G, g = blockIdx.x / G;
+    if (g >= ng) return {0, 0, G, 0};  // blocks past the last whole group: no items
+    const long long T = (long long)(tiles / G) * sc;
+    return {T * g / ng, T * (g + 1) / ng, G, (int)(blockIdx.x % G)};
 }
 
 // ---------------------------------------------------------------- unpack ---
@@ -369,10 +388,10 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *data = reinterpret_cast<T *>(smem_raw);  // [PT][N2][C]
     float2 *tws = reinterpret_cast<float2 *>(data + PT * p.N2 * p.C);  // [N2][C], then (PFB) raw frames
-    const Span sp = block_span(p.tiles, p.sc);
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
     for (long long f = sp.lo; f < sp.hi;) {
-        const int x = (int)(f / p.sc);
-        const long long base = (long long)x * p.sc;
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         // the barrier after the first batch's FIR orders the twiddle tile's
         // stores before their use; col_fft_store ends on a barrier, so the
@@ -426,10 +445,10 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
     const int D = PT - p.P;                                            // leading zero taps
     // first-pass twiddles W_N2^(j q) (ordered before use by the loop's barriers)
     for (int e = t; e < G::TWC; e += blockDim.x) twc[e] = __ldg(p.twA + p.pass[0].off + e);
-    const Span sp = block_span(p.tiles, p.sc);
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
     for (long long f = sp.lo; f < sp.hi;) {
-        const int x = (int)(f / p.sc);
-        const long long base = (long long)x * p.sc;
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
@@ -564,10 +583,10 @@ __global__ void __launch_bounds__(512) fir_colfft_gather_kernel(const __grid_con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *data = reinterpret_cast<T *>(smem_raw);  // [N2][C]
     float2 *tws = reinterpret_cast<float2 *>(data + p.N2 * p.C);  // [N2][C]
-    const Span sp = block_span(p.tiles, p.sc);
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
     for (long long f = sp.lo; f < sp.hi;) {
-        const int x = (int)(f / p.sc);
-        const long long base = (long long)x * p.sc;
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
