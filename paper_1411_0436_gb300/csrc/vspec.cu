@@ -206,6 +206,24 @@ template <int NPOL> const void *pick_kernel_a(int PT, int PPT) {
     return nullptr;
 }
 
+// register-column kernel A for dual-pol direct FFT (2048-point tiles), N2 in
+// 2 .. 256, and its column pass list (one pass up to 16 points, then 16 x N2/16)
+const void *pick_kernel_coldir(int N2, size_t *smem, std::vector<int> *radices) {
+    using namespace vspec;
+    *radices = N2 <= 16 ? std::vector<int>{N2} : std::vector<int>{16, N2 / 16};
+    switch (N2) {
+        case 2: *smem = ColDir<2>::smem; return (const void *)fir_coldir_kernel<2>;
+        case 4: *smem = ColDir<4>::smem; return (const void *)fir_coldir_kernel<4>;
+        case 8: *smem = ColDir<8>::smem; return (const void *)fir_coldir_kernel<8>;
+        case 16: *smem = ColDir<16>::smem; return (const void *)fir_coldir_kernel<16>;
+        case 32: *smem = ColDir<32>::smem; return (const void *)fir_coldir_kernel<32>;
+        case 64: *smem = ColDir<64>::smem; return (const void *)fir_coldir_kernel<64>;
+        case 128: *smem = ColDir<128>::smem; return (const void *)fir_coldir_kernel<128>;
+        case 256: *smem = ColDir<256>::smem; return (const void *)fir_coldir_kernel<256>;
+    }
+    return nullptr;
+}
+
 // register-column kernel A (dual-pol PFB, 8 taps, 512-point tiles) for N2 in
 // 2 .. 64 and its column pass list (one pass up to 16 points, then 8 x N2/8)
 const void *pick_kernel_colreg(int N2, size_t *smem, std::vector<int> *radices) {
@@ -543,6 +561,13 @@ vspec_status build_plan(vspec_plan *p) {
     const int pts_target = PT == 1 ? 4096 : 512;
     int C = std::max(cmin, pts_target / N2);
     C = std::min(C, N1);
+    // dual-pol direct FFT with 2048-point rows: the register-column kernel A
+    // in tiles of 2048 points
+    size_t smem_coldir = 0;
+    std::vector<int> r_coldir;
+    const void *coldir = p->npol == 2 && !pfb && N1 == 2048 && N2 >= 2 && N2 <= 256
+                             ? pick_kernel_coldir(N2, &smem_coldir, &r_coldir) : nullptr;
+    if (coldir) C = 2048 / N2;
     const int pts = N2 * C;
     const int TA = std::min(512, pts);
     const int PPT = pts / TA;
@@ -557,6 +582,7 @@ vspec_status build_plan(vspec_plan *p) {
     p->TA = TA;
     p->kernelA = p->gather ? (p->npol == 2 ? pick_kernel_gather<2>(PPT) : pick_kernel_gather<1>(PPT))
                            : (p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT));
+    if (coldir) p->kernelA = coldir;
     if (!p->kernelA) {
         g_last_error = "no kernel instance for this tap count and size";
         return VSPEC_ERR_UNSUPPORTED;
@@ -582,7 +608,8 @@ vspec_status build_plan(vspec_plan *p) {
     const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512
                              ? pick_kernel_colreg(N2, &smem_colreg, &r_colreg) : nullptr;
     if (colreg) p->kernelA = colreg;
-    const std::vector<int> rA = colreg ? r_colreg : radix_list(e2, maxbitsA), rB = radix_list(e1);
+    const std::vector<int> rA = colreg ? r_colreg : coldir ? r_coldir : radix_list(e2, maxbitsA),
+                           rB = radix_list(e1);
     int twA_n = 0, twB_n = 0;
     p->passA = make_passes(N2, rA, &twA_n);
     p->passB = make_passes(N1, rB, &twB_n);
@@ -622,6 +649,7 @@ vspec_status build_plan(vspec_plan *p) {
     p->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2) +
                (!p->gather ? 2 * (size_t)PT * N2 * C * p->npol * 2 : 0);
     if (colreg) p->smemA = smem_colreg;
+    if (coldir) p->smemA = smem_coldir;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
     if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);
@@ -753,8 +781,8 @@ vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps, int npol,
 // 0.62 of it with an 8-tap PFB, 0.70 in direct mode). With only a few idle
 // SMs the second path's fixed cost outweighs them.
 constexpr int kTwoKernelFrom[2][5] = {
-    {INT_MAX, 900, 300, 100, 0},   // PFB, nchan 2048 .. 32768
-    {INT_MAX, 1500, 400, 130, 90}  // direct
+    {INT_MAX, 800, 300, 100, 0},  // PFB, nchan 2048 .. 32768
+    {INT_MAX, 900, 300, 100, 70}  // direct
 };
 constexpr double kAssistPerSmRate = 0.62;        // PFB
 constexpr double kAssistPerSmRateDirect = 0.70;  // direct FFT
@@ -1053,6 +1081,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     for (int i = 0; i < ca.npass; i++) ca.pass[i] = p->passA[i];
     ca.tiles = p->N1 / p->C;
     ca.G = p->tileG;
+    ca.win = p->mode == VSPEC_DIRECT && p->window != VSPEC_WIN_RECT;
 
     vspec::RowParams cb{};
     cb.Z = p->Z;

@@ -53,6 +53,7 @@ struct ColParams {
     int sc;              // spectra in this chunk
     int tiles;           // column tiles, N1 / C
     int G;               // tiles per group (tile_split); 0 or 1: no groups
+    int win;             // direct mode with a window: multiply by coef (register-column kernels)
 };
 
 struct RowParams {
@@ -569,6 +570,145 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
             }
         }
         __syncthreads();  // the column passes are done with the twiddle tile
+    }
+}
+
+// Kernel A, register-column form for dual-pol direct FFT (no pre-filter):
+// tiles of C = 2048 / N2 columns, N2 = 2 .. 256. SPB spectra per batch; their
+// int8 frames are staged into shared memory one batch ahead. Columns of at
+// most 16 points are whole DFTs in registers straight from the staged bytes
+// (one pass, natural output order); longer columns take two DIF passes,
+// radix 16 then N2 / 16 (the plan's column pass list {16, N2/16}): the first
+// reads the staged bytes and writes fp32 to shared memory, the second writes
+// the chunk scratch. Every output is multiplied by W_N^(n1 k2) on its way out.
+template <int N2>
+struct ColDir {
+    static constexpr int PTS = 2048, C = PTS / N2, SPB = 4;
+    static constexpr bool kOnePass = N2 <= 16;
+    static constexpr int R1 = kOnePass ? N2 : 16, R2 = N2 / R1, M1 = N2 / R1;
+    static constexpr int CPT = SPB * C / 512;                // columns per thread (one pass)
+    static constexpr int B1 = SPB * C * M1 / 512;            // first-pass butterflies per thread
+    static constexpr int B2 = SPB * C * R1 / 512;            // second-pass butterflies per thread
+    static constexpr int TWC = kOnePass ? 0 : M1 * (R1 - 1);  // first-pass twiddles
+    // raw frames [2][SPB][PTS] u32, data [SPB][PTS] P2 (two-pass form),
+    // twiddle tile [N2][C] float2, first-pass twiddles [TWC] float2, window
+    // values of the tile [N2][C] float
+    static constexpr size_t smem = 2 * (size_t)SPB * PTS * 4 + (kOnePass ? 0 : (size_t)SPB * PTS * 16) +
+                                   (size_t)PTS * 8 + (size_t)TWC * 8 + (size_t)PTS * 4;
+    static_assert(N2 >= 2 && N2 <= 256 && C >= 8, "column shapes of this kernel");
+};
+
+template <int N2>
+__global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__ ColParams p) {
+    using G = ColDir<N2>;
+    constexpr int PTS = G::PTS, C = G::C, SPB = G::SPB, R1 = G::R1, R2 = G::R2, M1 = G::M1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *raw = reinterpret_cast<uint32_t *>(smem_raw);                        // [2][SPB][PTS]
+    P2 *data = reinterpret_cast<P2 *>(raw + 2 * SPB * PTS);                        // [SPB][PTS]
+    float2 *tws = reinterpret_cast<float2 *>(data + (G::kOnePass ? 0 : SPB * PTS));  // [N2][C]
+    float2 *twc = tws + PTS;                                                       // [M1][R1-1]
+    float *wins = reinterpret_cast<float *>(twc + G::TWC);                         // [N2][C]
+    const int t = threadIdx.x;
+    for (int e = t; e < G::TWC; e += blockDim.x) twc[e] = __ldg(p.twA + p.pass[0].off + e);
+    // sample (pos e of the tile) of spectrum row rb, times the window value when there is one
+    auto sample = [&](const uint32_t *rb, int e) {
+        P2 v = unpack_p2(rb[e] ^ 0x80808080u);
+        if (p.win) {
+            const float2 h = dup2(wins[e]);
+            v = P2{__fmul2_rn(v.re, h), __fmul2_rn(v.im, h)};
+        }
+        return v;
+    };
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        const int n1_0 = x * C;
+        for (int e = t; e < PTS; e += blockDim.x) {  // W_N^(n1 k2(pos)); window values h[n1 + N1 n2]
+            tws[e] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
+            if (p.win) wins[e] = __ldg(p.coef + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
+        }
+        // frames of SPB spectra into raw[buf], 16-byte copies
+        auto stage = [&](int sb, int buf) {
+            const int nbb = min(SPB, s_end - sb);
+            constexpr int per_row = C / 4, per_frame = PTS / 4;
+            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
+                const int u = e / per_frame, r = e % per_frame;
+                const int n2 = r / per_row, ch = r % per_row;
+                const long long fr = p.s0 + sb + u;
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
+                                      (long long)p.N1 * n2 + ch * 4;
+                uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        stage(s_beg, 0);
+        for (int s_base = s_beg, buf = 0; s_base < s_end; s_base += SPB, buf ^= 1) {
+            const int nb = min(SPB, s_end - s_base);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // frames and the twiddle tile visible; the other buffer and data are free
+            if (s_base + SPB < s_end) stage(s_base + SPB, buf ^ 1);
+            const uint32_t *rb = raw + buf * SPB * PTS;
+            if constexpr (G::kOnePass) {
+#pragma unroll
+                for (int k = 0; k < G::CPT; k++) {
+                    const int col = t + k * 512;  // = sb * C + c
+                    const int sb = col / C, c = col % C;
+                    if (sb < nb) {
+                        P2 v[N2];
+#pragma unroll
+                        for (int q = 0; q < N2; q++) v[q] = sample(rb + sb * PTS, q * C + c);
+                        Dft<N2>::run(v);
+                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        z[0] = v[0];
+#pragma unroll
+                        for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
+                    }
+                }
+            } else {
+                // first pass: butterfly j of column (sb, c) over positions j + M1 q
+#pragma unroll
+                for (int k = 0; k < G::B1; k++) {
+                    const int e = t + k * 512;
+                    const int c = e % C, j = (e / C) % M1, sb = e / (C * M1);
+                    if (sb < nb) {
+                        const int o = sb * PTS + j * C + c;
+                        P2 v[R1];
+#pragma unroll
+                        for (int q = 0; q < R1; q++) v[q] = sample(rb + sb * PTS, (j + q * M1) * C + c);
+                        Dft<R1>::run(v);
+                        const float2 *w = twc + j * (R1 - 1);
+                        data[o] = v[0];
+#pragma unroll
+                        for (int q = 1; q < R1; q++) data[o + q * M1 * C] = cmul(v[q], w[q - 1]);
+                    }
+                }
+                __syncthreads();
+                // second pass: block b of column (sb, c), positions b R2 + q, to the scratch
+#pragma unroll
+                for (int k = 0; k < G::B2; k++) {
+                    const int e = t + k * 512;
+                    const int c = e % C, b = (e / C) % R1, sb = e / (C * R1);
+                    if (sb < nb) {
+                        const P2 *d = data + sb * PTS + b * R2 * C + c;
+                        P2 v[R2];
+#pragma unroll
+                        for (int q = 0; q < R2; q++) v[q] = d[q * C];
+                        Dft<R2>::run(v);
+                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
+                                (size_t)(b * R2) * p.N1 + n1_0 + c;
+#pragma unroll
+                        for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[(b * R2 + q) * C + c]);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the column passes are done with the twiddle tile and data
     }
 }
 
