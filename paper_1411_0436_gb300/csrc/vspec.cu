@@ -308,12 +308,12 @@ vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 g
 }
 
 // Fold `slots` partial-sum slots of p->partial (and p->partial_comp in
-// compensated plans) into d_accum: with more than 48 slots, first sum each
+// compensated plans) into d_accum: with more than 128 slots, first sum each
 // group of 16 slots into its first slot, then fold the group sums.
 vspec_status launch_fold(vspec_plan *p, int slots, float *d_accum, int spectra, cudaStream_t st) {
     int groups = slots, stride = 1;
     const int N = p->N, N1 = p->N1, N2 = p->N2;
-    if (slots > 48) {
+    if (slots > 128) {
         groups = (slots + 15) / 16;
         stride = 16;
         const void *fold = p->npol == 2 ? (p->kahan ? (const void *)vspec::fold_slots_kernel<2, true>
@@ -652,6 +652,12 @@ vspec_status build_plan(vspec_plan *p) {
     if (coldir) p->smemA = smem_coldir;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
+    if (p->fir_b)  // one-row transform: frame ring and coefficients (general row kernel)
+        p->smemB = (p->npol == 2 ? (p->kahan ? vspec::row_ring_offset<2, true>(p->RB, N1)
+                                             : vspec::row_ring_offset<2, false>(p->RB, N1))
+                                 : (p->kahan ? vspec::row_ring_offset<1, true>(p->RB, N1)
+                                             : vspec::row_ring_offset<1, false>(p->RB, N1))) +
+                   vspec::row_ring_bytes(p->npol, p->P, N1);
     if (p->tc) p->smemB = vspec::tc_rowfft_smem(p->kahan);
     // 2048-point rows (radix 16, 16, 8): the paired-spectra row kernel with
     // register accumulators
@@ -1060,8 +1066,12 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     const int sc_full = (nspectra + nchunks - 1) / nchunks;
     // slots of the largest kernel-B launch (no more CTAs than items)
     const int tilesB = p->N2 / p->RB;
-    const int slots = slots_for(p, (int)std::min<long long>(nB, (long long)tilesB * sc_full));
-    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
+    int slots = slots_for(p, (int)std::min<long long>(nB, (long long)tilesB * sc_full));
+    // a one-row transform in one launch: block k is the only writer of slot k
+    // and stores it, so nothing needs zeroing and the fold reads those slots
+    const bool store = p->fir_b && !p->kahan && !p->tc && nchunks == 1;
+    if (store) slots = (int)std::min<long long>(nB, (long long)tilesB * sc_full);
+    if (!store) VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
     if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
 
     vspec::ColParams ca{};
@@ -1101,6 +1111,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     cb.in = d_in;
     cb.coef = p->coef;
     cb.P = p->P;
+    cb.store = store;
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);

@@ -73,6 +73,7 @@ struct RowParams {
     const float *coef;
     int P;
     long long s0;        // absolute index of the chunk's first spectrum
+    int store;           // 1: every slot has exactly one writer this call, which stores (no zeroing)
 };
 
 // ------------------------------------------------------------ work split --
@@ -333,7 +334,6 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
         // the FIR of one spectrum of the batch (slot u of the window rotation)
         auto fir_one = [&](auto uc) {
             constexpr int u = decltype(uc)::value;
-            const long long fnew = p.s0 + s_base + u + p.P - 1;  // newest frame of spectrum s_base + u
             constexpr int snew = (u + PT - 1) % PT;
 #pragma unroll
             for (int i = 0; i < PPT; i++) {
@@ -342,8 +342,8 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
                     const unsigned char *rs = raw + ((size_t)(buf * PT + u) * pts + sm_pt[i]) * B;
                     if constexpr (NPOL == 2) wx = *reinterpret_cast<const uint32_t *>(rs);
                     else wx = *reinterpret_cast<const unsigned short *>(rs);
-                } else {
-                    wx = load_raw<NPOL>(p.in, fnew * p.N + n_pt[i]);
+                } else {  // newest frame of spectrum s_base + u
+                    wx = load_raw<NPOL>(p.in, (p.s0 + s_base + u + p.P - 1) * p.N + n_pt[i]);
                 }
                 wx ^= 0x80808080u;
                 T *d = data + u * pts + sm_pt[i];
@@ -848,20 +848,46 @@ __device__ __forceinline__ typename Elem<NPOL>::T fir_sample(const RowParams &p,
     else return make_float2(a[0], a[1]);
 }
 
+// The same pre-filter output from frames staged in shared memory: ring slot
+// (slot0 + t) mod (P + 1) holds frame s + t as int8 (N1 samples), cfs[t N1 + n]
+// the coefficients h[t N + n] (one-row transforms, N = N1).
+template <int NPOL>
+__device__ __forceinline__ typename Elem<NPOL>::T fir_ring(const unsigned char *ring, const float *cfs, int N1,
+                                                           int P, int slot0, int n) {
+    constexpr int NC = 2 * NPOL;
+    float a[NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) a[k] = 0.f;
+    int slot = slot0;
+    for (int t = 0; t < P; t++) {
+        const float c = cfs[t * N1 + n];
+        uint32_t w;
+        if constexpr (NPOL == 2) w = reinterpret_cast<const uint32_t *>(ring)[slot * N1 + n];
+        else w = reinterpret_cast<const unsigned short *>(ring)[slot * N1 + n];
+        w ^= 0x80808080u;
+#pragma unroll
+        for (int k = 0; k < NC; k++) a[k] = fmaf(c, unpack_byte(w, k), a[k]);
+        slot = slot == P ? 0 : slot + 1;
+    }
+    if constexpr (NPOL == 2) return make_p2(a[0], a[1], a[2], a[3]);
+    else return make_float2(a[0], a[1]);
+}
+
 template <int R, int NPOL, bool KAHAN = false, bool FIR = false>
 __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::Acc *acc,
                                               const typename Elem<NPOL>::T *Zs, const Pass ps,
                                               bool first, bool last, int r, int b, int j,
                                               int rowstride, typename Elem<NPOL>::Acc *comp = nullptr,
-                                              long long sabs = 0) {
+                                              const unsigned char *ring = nullptr, const float *cfs = nullptr,
+                                              int slot0 = 0) {
     using T = typename Elem<NPOL>::T;
     const int base = b * ps.lb + j;
     T *row = data + r * rowstride;
     T v[R];
     if (FIR && first) {
 #pragma unroll
-        for (int q = 0; q < R; q++) v[q] = fir_sample<NPOL>(p, sabs, base + q * ps.m);
+        for (int q = 0; q < R; q++) v[q] = fir_ring<NPOL>(ring, cfs, p.N1, p.P, slot0, base + q * ps.m);
     } else if (first) {
         const T *zr = Zs + (size_t)(x * p.RB + r) * p.N1;
 #pragma unroll
@@ -897,6 +923,18 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typenam
     }
 }
 
+// Shared memory of the general row kernel: RB padded rows, the accumulators
+// (and their compensation), then, for one-row transforms, the frame ring and
+// coefficients at a 16-byte boundary.
+template <int NPOL, bool KAHAN>
+__host__ __device__ constexpr size_t row_ring_offset(int RB, int N1) {
+    return ((size_t)RB * (N1 + (N1 >> 4)) * sizeof(typename Elem<NPOL>::T) +
+            (size_t)RB * N1 * sizeof(typename Elem<NPOL>::Acc) * (KAHAN ? 2 : 1) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t row_ring_bytes(int npol, int P, int N1) {
+    return (size_t)(P + 1) * N1 * 2 * npol + (size_t)P * N1 * 4;
+}
+
 template <int NPOL, bool KAHAN = false, bool FIR = false>
 __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_constant__ RowParams p) {
     using T = typename Elem<NPOL>::T;
@@ -910,6 +948,22 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
     const int RL = p.pass[p.npass - 1].r;
     const int lq = p.lN1 - p.pass[p.npass - 1].lr;  // log2 (N1 / RL)
     const int lU = p.lRB + lq;
+    // one-row transforms (FIR): a ring of P + 1 int8 frames and the P taps'
+    // coefficients in shared memory, filled with 16-byte asynchronous copies;
+    // the frame of the next spectrum is copied while this one is transformed
+    constexpr int W = 2 * NPOL;  // bytes per sample
+    unsigned char *ring = smem_raw + row_ring_offset<NPOL, KAHAN>(p.RB, p.N1);
+    float *cfs = reinterpret_cast<float *>(ring + (FIR ? (size_t)(p.P + 1) * p.N1 * W : 0));
+    auto copy16 = [&](void *dst, const void *src, int bytes) {
+        for (int e = threadIdx.x; e < bytes / 16; e += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"((uint32_t)__cvta_generic_to_shared(static_cast<unsigned char *>(dst) + 16 * e)),
+                            "l"(static_cast<const unsigned char *>(src) + 16 * e) : "memory");
+    };
+    auto stage_frame = [&](long long fr) {  // frame fr into slot fr mod (P + 1)
+        copy16(ring + (size_t)(fr % (p.P + 1)) * p.N1 * W, p.in + fr * p.N * W, p.N1 * W);
+    };
+    if constexpr (FIR) copy16(cfs, p.coef, p.P * p.N1 * 4);
 
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
@@ -924,10 +978,27 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
             else acc[e] = 0.f;
             if constexpr (KAHAN) comp[e] = acc[e];
         }
+        if constexpr (FIR) {  // the segment's first spectrum's P frames
+            for (int t = 0; t < p.P; t++) stage_frame(p.s0 + s_beg + t);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
         __syncthreads();
 
         for (int s = s_beg; s < s_end; s++) {
             const T *Zs = FIR ? nullptr : reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N;
+            if constexpr (FIR) {
+                // the next spectrum's newest frame takes the slot of frame s - 1,
+                // which the previous spectrum's passes are done with
+                if (s + 1 < s_end) {
+                    stage_frame(p.s0 + s + p.P);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                }
+                __syncthreads();  // spectrum s's frames are visible to every thread
+            }
+            const int slot0 = FIR ? (int)((p.s0 + s) % (p.P + 1)) : 0;
             for (int ip = 0; ip < p.npass; ip++) {
                 const Pass ps = p.pass[ip];
                 const bool first = ip == 0, last = ip == p.npass - 1;
@@ -936,12 +1007,11 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
                 for (int u = threadIdx.x; u < nb; u += blockDim.x) {
                     const int r = u >> lper, w = u & ((1 << lper) - 1);
                     const int b = w >> ps.lm, j = w & (ps.m - 1);
-                    const long long sabs = p.s0 + s;
                     switch (ps.r) {
-                        case 2: row_butterfly<2, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
-                        case 4: row_butterfly<4, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
-                        case 8: row_butterfly<8, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
-                        default: row_butterfly<16, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, sabs); break;
+                        case 2: row_butterfly<2, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, ring, cfs, slot0); break;
+                        case 4: row_butterfly<4, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, ring, cfs, slot0); break;
+                        case 8: row_butterfly<8, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, ring, cfs, slot0); break;
+                        default: row_butterfly<16, NPOL, KAHAN, FIR>(p, x, data, acc, Zs, ps, first, last, r, b, j, rowstride, comp, ring, cfs, slot0); break;
                     }
                 }
                 __syncthreads();
@@ -963,6 +1033,8 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
                 else kahan_add(a, c, acc[e] - comp[e]);
                 part[o] = a;
                 pc[o] = c;
+            } else if (p.store) {
+                part[o] = acc[e];
             } else if constexpr (NPOL == 2) {
                 float4 a = part[o];
                 const float4 d = acc[e];
@@ -1095,6 +1167,8 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
                 else kahan_add(a, c, acc[q] - comp[q]);
                 part[q] = a;
                 pc[q] = c;
+            } else if (p.store) {
+                part[q] = acc[q];
             } else if constexpr (NPOL == 2) {
                 const float4 a = part[q];
                 part[q] = make_float4(a.x + acc[q].x, a.y + acc[q].y, a.z + acc[q].z, a.w + acc[q].w);
