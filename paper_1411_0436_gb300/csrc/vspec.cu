@@ -225,7 +225,7 @@ const void *pick_kernel_coldir(int N2, size_t *smem, std::vector<int> *radices) 
 }
 
 // register-column kernel A (dual-pol PFB, 8 taps, 512-point tiles) for N2 in
-// 2 .. 64 and its column pass list (one pass up to 16 points, then 8 x N2/8)
+// 2 .. 128 and its column pass list (one pass up to 16 points, then 8 x N2/8)
 const void *pick_kernel_colreg(int N2, size_t *smem, std::vector<int> *radices) {
     using namespace vspec;
     *radices = N2 <= 16 ? std::vector<int>{N2} : std::vector<int>{8, N2 / 8};
@@ -236,6 +236,7 @@ const void *pick_kernel_colreg(int N2, size_t *smem, std::vector<int> *radices) 
         case 16: *smem = ColReg<16>::smem; return (const void *)fir_colreg_kernel<16>;
         case 32: *smem = ColReg<32, 8>::smem; return (const void *)fir_colreg_kernel<32, 8>;
         case 64: *smem = ColReg<64, 8>::smem; return (const void *)fir_colreg_kernel<64, 8>;
+        case 128: *smem = ColReg<128, 8>::smem; return (const void *)fir_colreg_kernel<128, 8>;
     }
     return nullptr;
 }
@@ -568,6 +569,11 @@ vspec_status build_plan(vspec_plan *p) {
     const void *coldir = p->npol == 2 && !pfb && N1 == 2048 && N2 >= 2 && N2 <= 256
                              ? pick_kernel_coldir(N2, &smem_coldir, &r_coldir) : nullptr;
     if (coldir) C = 2048 / N2;
+    // dual-pol PFB (5 .. 8 taps) with 2048-point rows: the register-column
+    // kernel A in 512-point tiles (for N2 = 128 rows of 4 samples, which the
+    // tile groups read a whole line at a time)
+    const bool colreg_tiles = p->npol == 2 && pfb && PT == 8 && !p->gather && N1 == 2048 && N2 >= 2 && N2 <= 128;
+    if (colreg_tiles) C = 512 / N2;
     const int pts = N2 * C;
     const int TA = std::min(512, pts);
     const int PPT = pts / TA;

@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
 }
 
 // Kernel A, register-column form: dual-pol PFB of at most 8 taps in tiles of
-// 512 points (one per thread) with columns of N2 = 2 .. 64 points (nchan
-// 2^12 .. 2^17 with 2048-point rows). The FIR stage is the same register
+// 512 points (one per thread) with columns of N2 = 2 .. 128 points (nchan
+// 2^12 .. 2^18 with 2048-point rows). The FIR stage is the same register
 // window as above. Columns of at most 16 points (R1 == N2) are then whole
 // length-N2 DFTs in registers, one column per thread, in natural output
 // order (the plan's column pass list is the single radix-N2 pass, so
@@ -420,7 +420,9 @@ struct ColReg {
     static constexpr int PT = 8, PTS = 512, C = PTS / N2;
     static constexpr bool kOnePass = R1 == N2;
     static constexpr int R2 = N2 / R1;  // second-pass radix (two-pass form)
-    static constexpr int SPB = kOnePass && N2 > PT ? N2 : PT;
+    // spectra per column stage: enough that each pass has a butterfly per thread
+    static constexpr int SPB = kOnePass ? (N2 > PT ? N2 : PT)
+                                        : (PTS / (C * (R1 < R2 ? R1 : R2)) > PT ? PTS / (C * (R1 < R2 ? R1 : R2)) : PT);
     static constexpr int CPT = SPB * C / PTS;             // columns per thread (one pass)
     static constexpr int B1 = SPB * C * (N2 / R1) / PTS;  // first-pass butterflies per thread
     static constexpr int B2 = SPB * C * R1 / PTS;         // second-pass butterflies per thread
@@ -429,7 +431,8 @@ struct ColReg {
     // u32, coefficients [PT][PTS] float, first-pass twiddles [TWC] float2
     static constexpr size_t smem = (size_t)SPB * PTS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 +
                                    (size_t)PT * PTS * 4 + (size_t)TWC * 8;
-    static_assert(kOnePass ? N2 <= 16 : (R1 == 8 && (N2 == 32 || N2 == 64)), "column shapes of this kernel");
+    static_assert(kOnePass ? N2 <= 16 : (R1 == 8 && (N2 == 32 || N2 == 64 || N2 == 128)), "column shapes of this kernel");
+    static_assert(B1 * PTS == SPB * C * (N2 / R1) && B2 * PTS == SPB * C * R1, "whole butterflies per thread");
 };
 
 template <int N2, int R1 = N2>
