@@ -790,12 +790,15 @@ __device__ __forceinline__ float4 detect4(P2 v) {
     const float2 p = __ffma2_rn(v.re, v.re, __fmul2_rn(v.im, v.im));  // (|X|^2, |Y|^2)
     return make_float4(p.x, p.y, fmaf(v.re.x, v.re.y, v.im.x * v.im.y), fmaf(v.im.x, v.re.y, -(v.re.x * v.im.y)));
 }
+// a += detect4(v), each product accumulated by a fused multiply-add
+// (|X|^2 and |Y|^2 as one pair)
 template <int NPOL> __device__ __forceinline__ void acc_add(float4 &a, P2 v) {
-    const float4 d = detect4(v);
-    a.x += d.x;
-    a.y += d.y;
-    a.z += d.z;
-    a.w += d.w;
+    float2 xy = __ffma2_rn(v.im, v.im, make_float2(a.x, a.y));
+    xy = __ffma2_rn(v.re, v.re, xy);
+    a.x = xy.x;
+    a.y = xy.y;
+    a.z = fmaf(v.re.x, v.re.y, fmaf(v.im.x, v.im.y, a.z));
+    a.w = fmaf(v.im.x, v.re.y, fmaf(-v.re.x, v.im.y, a.w));
 }
 __device__ __forceinline__ void acc_add1(float &a, float2 v) { a += fmaf(v.x, v.x, v.y * v.y); }
 

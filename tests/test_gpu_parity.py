@@ -74,6 +74,18 @@ SMALL = [
     (1 << 20, 16, 1, PFB, WIN_HANN, 2),
     (1 << 20, 1, 1, DIRECT, WIN_RECT, 2),  # single-pol, 32-byte column segments
     (1 << 18, 16, 2, PFB, WIN_HANN, 3),
+    # register-column kernel A: every column shape, windows, fewer taps than
+    # the register window (leading zero taps)
+    (8192, 8, 2, PFB, WIN_HANN, 9),        # 4-point columns, two per thread
+    (32768, 5, 2, PFB, WIN_RECT, 9),       # 16-point columns, 3 zero taps
+    (131072, 8, 2, PFB, WIN_HANN, 5),      # 64-point columns, passes 8 x 8
+    (262144, 6, 2, PFB, WIN_HAMMING, 3),   # 128-point columns, 4-sample tile rows
+    (16384, 1, 2, DIRECT, WIN_HANN, 17),   # direct, 8-point columns, window
+    (65536, 1, 2, DIRECT, WIN_HAMMING, 5), # direct, passes 16 x 2, window
+    (262144, 1, 2, DIRECT, WIN_HANN, 3),   # direct, passes 16 x 8, window
+    # one-row transforms: frame ring with the most taps, and with one
+    (1024, 16, 2, PFB, WIN_HANN, 21),
+    (512, 1, 1, DIRECT, WIN_HAMMING, 7),
 ]
 
 
