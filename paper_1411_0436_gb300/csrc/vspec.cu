@@ -607,7 +607,7 @@ vspec_status build_plan(vspec_plan *p) {
     // the butterfly width so both fit in 128 registers.
     const int capA = vspec::col_radix_cap(p->npol, PT, PPT);
     const int maxbitsA = capA == 16 ? 4 : capA == 8 ? 3 : 2;
-    // dual-pol PFB (5 .. 8 taps) with columns of 2 .. 64 points in 512-point
+    // dual-pol PFB (5 .. 8 taps) with columns of 2 .. 128 points in 512-point
     // tiles: the register-column kernel A and its own column pass list
     size_t smem_colreg = 0;
     std::vector<int> r_colreg;

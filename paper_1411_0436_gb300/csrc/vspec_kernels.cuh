@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
 // window as above. Columns of at most 16 points (R1 == N2) are then whole
 // length-N2 DFTs in registers, one column per thread, in natural output
 // order (the plan's column pass list is the single radix-N2 pass, so
-// pos = k2). Longer columns take two DIF passes, radix R1 then N2 / R1, the
-// plan's pass list {R1, N2/R1}, with every index a compile-time function of
+// pos = k2). Longer columns take two DIF passes, radix R1 = 8 then N2 / 8,
+// the plan's pass list {8, N2/8}, with every index a compile-time function of
 // the thread: the first pass's twiddles come from a small table in shared
 // memory, the second pass writes the chunk scratch. Every output is
 // multiplied by W_N^(n1 k2) on its way out. SPB spectra share a column
@@ -427,10 +427,18 @@ struct ColReg {
     static constexpr int B1 = SPB * C * (N2 / R1) / PTS;  // first-pass butterflies per thread
     static constexpr int B2 = SPB * C * R1 / PTS;         // second-pass butterflies per thread
     static constexpr int TWC = kOnePass ? 0 : (N2 / R1) * (R1 - 1);  // first-pass twiddles
-    // data [SPB][PTS] P2, twiddle tile [N2][C] float2, raw frames [2][SPB][PTS]
+    // Narrow tiles (C < 8 in the two-pass form): an 8-lane phase of the second
+    // pass spans 8 / C blocks b, C * R2 elements apart; C pad elements after
+    // every C * R2 put them in different banks. Element i of a spectrum is at
+    // pad(i); a spectrum takes SS elements.
+    static constexpr int PADG = !kOnePass && C < 8 ? C * R2 : 0, PADW = C;
+    static constexpr int SS = PTS + (PADG ? PTS / PADG * PADW : 0);
+    __device__ static constexpr int pad(int i) { return PADG ? i + i / PADG * PADW : i; }
+    // data [SPB][SS] P2, twiddle tile [N2][C] float2, raw frames [2][SPB][PTS]
     // u32, coefficients [PT][PTS] float, first-pass twiddles [TWC] float2
-    static constexpr size_t smem = (size_t)SPB * PTS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 +
+    static constexpr size_t smem = (size_t)SPB * SS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 +
                                    (size_t)PT * PTS * 4 + (size_t)TWC * 8;
+    static_assert(smem <= 232448, "shared memory of one CTA");
     static_assert(kOnePass ? N2 <= 16 : (R1 == 8 && (N2 == 32 || N2 == 64 || N2 == 128)), "column shapes of this kernel");
     static_assert(B1 * PTS == SPB * C * (N2 / R1) && B2 * PTS == SPB * C * R1, "whole butterflies per thread");
 };
@@ -440,8 +448,9 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
     using G = ColReg<N2, R1>;
     constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][PTS]
-    float2 *tws = reinterpret_cast<float2 *>(data + SPB * PTS);        // [N2][C]
+    constexpr int SS = G::SS;
+    P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][SS]
+    float2 *tws = reinterpret_cast<float2 *>(data + SPB * SS);         // [N2][C]
     uint32_t *raw = reinterpret_cast<uint32_t *>(tws + PTS);           // [2][SPB][PTS]
     float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);       // [PT][PTS]
     float2 *twc = reinterpret_cast<float2 *>(cfs + PT * PTS);          // [N2/R1][R1-1]
@@ -512,7 +521,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                     y.re = __ffma2_rn(cf2[k], wk.re, y.re);
                     y.im = __ffma2_rn(cf2[k], wk.im, y.im);
                 }
-                data[u * PTS + t] = y;
+                data[u * SS + G::pad(t)] = y;
             };
             if (nb == SPB) for_slots(fir_one, std::make_integer_sequence<int, SPB>{});
             else for_slots_below(fir_one, nb, std::make_integer_sequence<int, SPB>{});
@@ -525,7 +534,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                     if (sb < nb) {
                         P2 v[N2];
 #pragma unroll
-                        for (int q = 0; q < N2; q++) v[q] = data[sb * PTS + q * C + c];
+                        for (int q = 0; q < N2; q++) v[q] = data[sb * SS + q * C + c];
                         Dft<N2>::run(v);
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
                         z[0] = v[0];
@@ -541,15 +550,15 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                     const int e = t + k * PTS;
                     const int c = e % C, j = (e / C) % M1, sb = e / (C * M1);
                     if (sb < nb) {
-                        P2 *d = data + sb * PTS + j * C + c;
+                        P2 *d = data + sb * SS + j * C + c;  // + pad((j C + c) + q M1 C) - (j C + c)
                         P2 v[R1];
 #pragma unroll
-                        for (int q = 0; q < R1; q++) v[q] = d[q * M1 * C];
+                        for (int q = 0; q < R1; q++) v[q] = d[G::pad(q * M1 * C)];
                         Dft<R1>::run(v);
                         const float2 *w = twc + j * (R1 - 1);
                         d[0] = v[0];
 #pragma unroll
-                        for (int q = 1; q < R1; q++) d[q * M1 * C] = cmul(v[q], w[q - 1]);
+                        for (int q = 1; q < R1; q++) d[G::pad(q * M1 * C)] = cmul(v[q], w[q - 1]);
                     }
                 }
                 __syncthreads();
@@ -559,7 +568,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                     const int e = t + k * PTS;
                     const int c = e % C, b = (e / C) % R1, sb = e / (C * R1);
                     if (sb < nb) {
-                        const P2 *d = data + sb * PTS + b * R2 * C + c;
+                        const P2 *d = data + sb * SS + G::pad(b * R2 * C) + c;
                         P2 v[R2];
 #pragma unroll
                         for (int q = 0; q < R2; q++) v[q] = d[q * C];
