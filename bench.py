@@ -67,15 +67,15 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, spectra_per_launch: float):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def _traffic(config: str, kernel: str, spectra_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    ent = d.get(kernel)
+    ent = d.get(config, {}).get(kernel)
     if not ent or ent.get("source_hash") != source_hash():
         return None
     return float(ent["dram_bytes_per_spectrum"]) * spectra_per_launch
@@ -358,7 +358,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     name, launches, spectra, kms = dom
     achieved = (spectra * per_spec_bytes) / (kms * 1e-3) / 1e9
     spl = spectra / max(1, launches)
-    traffic = _traffic(name, spl)
+    traffic = _traffic(config, name, spl)
     path_bytes = args.steps * S * per_spec_bytes
     kernels = {r[0]: {"launches": r[1], "total_ms": round(r[3], 4),
                       "share": round(r[3] / max(1e-9, sum(q[3] for q in stats)), 4)} for r in stats}
