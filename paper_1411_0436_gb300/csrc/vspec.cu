@@ -569,10 +569,11 @@ vspec_status build_plan(vspec_plan *p) {
     const void *coldir = p->npol == 2 && !pfb && N1 == 2048 && N2 >= 2 && N2 <= 256
                              ? pick_kernel_coldir(N2, &smem_coldir, &r_coldir) : nullptr;
     if (coldir) C = 2048 / N2;
-    // dual-pol PFB (5 .. 8 taps) with 2048-point rows: the register-column
-    // kernel A in 512-point tiles (for N2 = 128 rows of 4 samples, which the
-    // tile groups read a whole line at a time)
-    const bool colreg_tiles = p->npol == 2 && pfb && PT == 8 && !p->gather && N1 == 2048 && N2 >= 2 && N2 <= 128;
+    // dual-pol PFB (5 .. 8 taps) with 2048-point rows (4096 at 2^19): the
+    // register-column kernel A in 512-point tiles (for N2 = 128 rows of 4
+    // samples, which the tile groups read a whole line at a time)
+    const bool colreg_tiles = p->npol == 2 && pfb && PT == 8 && !p->gather && (N1 == 2048 || N1 == 4096) && N2 >= 2 &&
+                              N2 <= 128;
     if (colreg_tiles) C = 512 / N2;
     const int pts = N2 * C;
     const int TA = std::min(512, pts);
