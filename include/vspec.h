@@ -224,6 +224,25 @@ VSPEC_API vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out
 VSPEC_API vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int *hbm_passes);
 
 /*
+ * The plan's decomposition and kernels as one line of text, for logs and
+ * tests, e.g. "two-kernel N1=2048 N2=16 C=32 A=colreg B=row2048 chunk=2048".
+ * Words:
+ *   fused K=<cluster CTAs>   the one-pass cluster kernel, then " | " and the
+ *                            two-kernel plan it switches to
+ *   two-kernel               the general path
+ *   A=colreg|coldir|general|gather|none   kernel A's form: register columns
+ *                            (dual-pol PFB), register columns (dual-pol
+ *                            direct), the general kernel, taps read from the
+ *                            input; none for one-row transforms
+ *   B=row2048|general|tensor kernel B's form
+ *   fir-in-B                 one-row transform: the FIR runs in kernel B
+ *   kahan                    compensated accumulation
+ * Writes at most len bytes including the terminating NUL (truncating).
+ * Errors: VSPEC_ERR_INVALID_ARG (plan or buf NULL, len 0).
+ */
+VSPEC_API vspec_status vspec_plan_describe(const vspec_plan *plan, char *buf, size_t len);
+
+/*
  * Instrumentation. With profiling enabled, vspec_execute records a pair of
  * CUDA events on its stream around every kernel it launches; with it
  * disabled (the default) no event is recorded. Enabling or disabling clears

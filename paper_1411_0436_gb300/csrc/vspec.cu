@@ -117,6 +117,8 @@ struct vspec_plan {
     int N = 0, P = 0, npol = 0, mode = 0, window = 0, device = 0;
     int N1 = 0, N2 = 0, C = 0, PT = 0, PPT = 0, TA = 0, RB = 0, TB = 0;
     int tileG = 1;                   // kernel-A tiles per group (tile_split)
+    const char *formA = "general";   // kernel A's form (vspec_plan_describe)
+    const char *formB = "general";   // kernel B's form
     int num_sms = 0, occA = 1, occB = 1;
     int sc_max = 1;                  // spectra per chunk
     int sc_cap = 1, slots_cap = 1;   // largest chunk a tuning may ask for; slots allocated
@@ -590,6 +592,8 @@ vspec_status build_plan(vspec_plan *p) {
     p->kernelA = p->gather ? (p->npol == 2 ? pick_kernel_gather<2>(PPT) : pick_kernel_gather<1>(PPT))
                            : (p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT));
     if (coldir) p->kernelA = coldir;
+    if (coldir) p->formA = "coldir";
+    if (p->gather) p->formA = "gather";
     if (!p->kernelA) {
         g_last_error = "no kernel instance for this tap count and size";
         return VSPEC_ERR_UNSUPPORTED;
@@ -614,7 +618,11 @@ vspec_status build_plan(vspec_plan *p) {
     std::vector<int> r_colreg;
     const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512
                              ? pick_kernel_colreg(N2, &smem_colreg, &r_colreg) : nullptr;
-    if (colreg) p->kernelA = colreg;
+    if (colreg) {
+        p->kernelA = colreg;
+        p->formA = "colreg";
+    }
+    if (p->fir_b) p->formA = "none";
     const std::vector<int> rA = colreg ? r_colreg : coldir ? r_coldir : radix_list(e2, maxbitsA),
                            rB = radix_list(e1);
     int twA_n = 0, twB_n = 0;
@@ -635,6 +643,7 @@ vspec_status build_plan(vspec_plan *p) {
             return VSPEC_ERR_UNSUPPORTED;
         }
         p->tc = true;
+        p->formB = "tensor";
         p->kernelB = (p->flags & VSPEC_PLAN_KAHAN) ? (const void *)vspec::rowfft_detect_tc_kernel<3, true>
                                                    : (const void *)vspec::rowfft_detect_tc_kernel<3, false>;
         p->TB = 256;
@@ -680,6 +689,7 @@ vspec_status build_plan(vspec_plan *p) {
                            : (f ? (const void *)row2048_kernel<1, false, true> : (const void *)row2048_kernel<1, false, false>);
         p->TB = 256;
         p->smemB = 2 * (size_t)kRow2048Stride * elem;
+        p->formB = "row2048";
     }
 
     VSPEC_CUDA(cudaGetDevice(&p->device));
@@ -908,6 +918,29 @@ vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int 
         const size_t zb = tk ? (size_t)tk->sc_max * tk->N * (tk->npol == 2 ? sizeof(float4) : sizeof(float2)) : 0;
         *hbm_passes = (tk && !tk->fir_b && zb > (size_t)l2 / 2) ? 2 : 1;
     }
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_describe(const vspec_plan *plan, char *buf, size_t len) {
+    if (!plan || !buf || len == 0) return VSPEC_ERR_INVALID_ARG;
+    auto two_kernel = [](const vspec_plan *t) {
+        std::string d = "two-kernel N1=" + std::to_string(t->N1) + " N2=" + std::to_string(t->N2) +
+                        " C=" + std::to_string(t->C) + " A=" + t->formA + " B=" + t->formB +
+                        " chunk=" + std::to_string(t->sc_max);
+        if (t->fir_b) d += " fir-in-B";
+        if (t->kahan) d += " kahan";
+        return d;
+    };
+    std::string d;
+    if (plan->fused) {
+        d = "fused K=" + std::to_string(plan->cluster);
+        if (plan->assist) d += " | " + two_kernel(plan->assist);
+    } else {
+        d = two_kernel(plan);
+    }
+    const size_t n = std::min(len - 1, d.size());
+    std::memcpy(buf, d.data(), n);
+    buf[n] = '\0';
     return VSPEC_OK;
 }
 

@@ -87,6 +87,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_dump.restype = i
         lib.vspec_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i)]
         lib.vspec_plan_info.restype = i
+        lib.vspec_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        lib.vspec_plan_describe.restype = i
         lib.vspec_plan_set_profiling.argtypes = [vp, i]
         lib.vspec_plan_set_profiling.restype = i
         lib.vspec_plan_kernel_stats.argtypes = [vp, i, i, ctypes.POINTER(cp), ctypes.POINTER(ctypes.c_longlong),
@@ -209,6 +211,14 @@ def vspec_plan_info(plan: int):
     return int(sb.value), int(hp.value)
 
 
+def vspec_plan_describe(plan: int) -> str:
+    buf = ctypes.create_string_buffer(256)
+    st = load().vspec_plan_describe(plan, buf, len(buf))
+    if st != OK:
+        raise VspecError(st, "vspec_plan_describe")
+    return buf.value.decode()
+
+
 def vspec_plan_set_profiling(plan: int, enable: bool) -> None:
     st = load().vspec_plan_set_profiling(plan, 1 if enable else 0)
     if st != OK:
@@ -327,6 +337,10 @@ class Plan:
 
     def info(self):
         return vspec_plan_info(self.handle)
+
+    def describe(self) -> str:
+        """The plan's decomposition and kernel forms (vspec_plan_describe)."""
+        return vspec_plan_describe(self.handle)
 
     def check(self) -> None:
         """Raise if a bounded device-side wait of this plan expired."""

@@ -66,3 +66,9 @@ def test_tuning_rejects_null_arguments(lib):
     t = vspec.VspecTuning(1, 0, 1, 0, 0)
     assert lib.vspec_plan_get_tuning(None, None, None) == vspec.ERR_INVALID_ARG
     assert lib.vspec_plan_set_tuning(None, ctypes.byref(t)) == vspec.ERR_INVALID_ARG
+
+
+def test_describe_rejects_null_arguments(lib):
+    import ctypes
+    buf = ctypes.create_string_buffer(8)
+    assert lib.vspec_plan_describe(None, buf, 8) == vspec.ERR_INVALID_ARG

@@ -504,3 +504,24 @@ def test_fused_assist_shares_match_oracle(oracle_mod, cfg):
             sa = stats["fir_colfft"][2]  # spectra the assist channelized
             assert sa in (0, s * share // 1000) and (share > 0 or sa == 0)
             assert stats["fused_channelize"][2] + sa == s
+
+
+@pytest.mark.parametrize("cfg,expect", [
+    ((32768, 8, 2, PFB, WIN_HANN, 0), ("fused K=16", "A=colreg", "N2=16", "B=row2048")),   # c2
+    ((524288, 1, 2, DIRECT, WIN_RECT, 0), ("two-kernel", "A=coldir", "N2=256", "B=row2048")),  # c3
+    ((131072, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N2=64", "C=8", "B=row2048")),         # c4
+    ((262144, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N2=128", "C=4")),
+    ((524288, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N1=4096", "B=general")),
+    ((1 << 20, 8, 2, PFB, WIN_HANN, 0), ("A=gather", "N1=2048")),
+    ((1024, 8, 1, PFB, WIN_HANN, 0), ("A=none", "fir-in-B", "B=general")),              # c1
+    ((65536, 4, 1, PFB, WIN_HANN, 0), ("A=general",)),
+])
+def test_plans_choose_the_intended_kernels(cfg, expect):
+    """The fast kernel forms are chosen where they apply (a silent fallback to
+    the general kernels would still match the oracle, only slower)."""
+    from paper_1411_0436_gb300.vspec import Plan
+    n, p, npol, mode, win, _ = cfg
+    with Plan(n, p, npol, mode, win) as plan:
+        d = plan.describe()
+    for word in expect:
+        assert word in d, (cfg, d)
