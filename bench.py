@@ -292,6 +292,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     in_bytes = x.nbytes
     n, S = bank.nchan, bank.nspectra
     plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window)
+    plan_desc = plan.describe()  # decomposition and kernel forms, for the JSON line
     d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).to(dev)
     acc = torch.zeros(plan.out_floats, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -524,6 +525,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "path_roofline": {"achieved": path_bytes / (total_ms * 1e-3) / 1e9 / world * world,
                               "frac": path_bytes / (total_ms * 1e-3) / 1e9 / peak},
             "kernels": kernels,
+            "plan": plan_desc,
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
