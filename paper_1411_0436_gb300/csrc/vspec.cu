@@ -421,9 +421,10 @@ vspec_status dev_alloc(void **ptr, size_t bytes, size_t *total) {
 // partial-sum flush per row tile, the FIR window's leading frames, the ends of
 // every launch); the intermediate's HBM round trip costs less than those at
 // this budget (on GB300 a 1000-spectrum 32768-channel call runs at 42 GHz in
-// 32 MiB chunks that stay in L2, 87 GHz in one 512 MiB chunk).
+// 32 MiB chunks that stay in L2, 87 GHz in one 512 MiB chunk; a 131072-channel
+// PFB call at 106 GHz in 1 GiB chunks, 111 GHz in 4 GiB ones).
 // A tuned chunk may grow the scratch up to kScratchCap.
-constexpr size_t kScratchBudget = 1024ull << 20;
+constexpr size_t kScratchBudget = 4096ull << 20;
 constexpr size_t kScratchCap = 4096ull << 20;
 constexpr int kMaxChunkSpectra = 8192;  // small nchan: a default chunk long enough
 constexpr int kMaxWaves = 4;    // largest tuned launch, in waves of CTAs

@@ -199,7 +199,7 @@ def test_error_paths_on_device():
         sb, hp = plan.info()
         assert sb > 0 and hp == 1  # one-row transform: FIR, FFT and detection in one kernel
     with vspec.Plan(131072, 8, 2, PFB, WIN_HANN) as plan:
-        assert plan.info()[1] == 2  # 512 MiB chunk scratch: the intermediate goes through HBM
+        assert plan.info()[1] == 2  # 4 GiB chunk scratch: the intermediate goes through HBM
         plan.tune(chunk_spectra=16)  # 32 MiB chunks stay in L2
         assert plan.info()[1] == 1
     with vspec.Plan(32768, 8, 2, PFB, WIN_HANN) as plan:
