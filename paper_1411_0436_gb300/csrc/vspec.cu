@@ -125,7 +125,7 @@ struct vspec_plan {
     int sc_alloc = 1;                // chunk spectra the scratch holds now
     int blocks_a = 0, blocks_b = 0;  // CTAs per kernel-A / kernel-B launch, 0: one wave
     bool fir_b = false;              // one-row transform: kernel B only, FIR in its first pass
-    bool fold2048 = false;           // the fold runs reduce2048_kernel (2048-point rows, N2 >= 64)
+    bool fold2048 = false;           // the fold runs reduce2048_kernel (2048-point rows, N2 >= 16)
     bool gather = false;             // long PFB: kernel A reads the FIR taps from the input
     size_t smemA = 0, smemB = 0;
     std::vector<Pass> passA, passB;
@@ -337,10 +337,14 @@ vspec_status launch_fold(vspec_plan *p, int slots, float *d_accum, int spectra, 
         void *argsR[] = {&part, &pcomp, &groups, &stride, (void *)&N, (void *)&N1, (void *)&N2, &ia, &ib, &outp, &ocomp};
         return launch(p, 2, spectra, p->kernelR, dim3((N + 31) / 32), dim3(32, 8), argsR, 0, st);
     }
-    if (p->fold2048) {  // 2048-point rows, N2 >= 64: coalesced through a tile
-        const void *k = p->npol == 2 ? (const void *)vspec::reduce2048_kernel<2> : (const void *)vspec::reduce2048_kernel<1>;
+    if (p->fold2048) {  // 2048-point rows, N2 >= 16: coalesced through a tile
+        using namespace vspec;
+        // 32 positions per CTA; for N2 < 64 8 positions and 4 slot lanes (more CTAs, shorter chains)
+        const bool wide = N2 >= 64;
+        const void *k = p->npol == 2 ? (wide ? (const void *)reduce2048_kernel<2, 32, 1> : (const void *)reduce2048_kernel<2, 8, 4>)
+                                     : (wide ? (const void *)reduce2048_kernel<1, 32, 1> : (const void *)reduce2048_kernel<1, 8, 4>);
         void *argsT[] = {&part, &groups, &stride, (void *)&N, (void *)&N2, &ia, &outp};
-        return launch(p, 2, spectra, k, dim3(4 * N2), dim3(256), argsT, 0, st);
+        return launch(p, 2, spectra, k, dim3(N2 / 16 * 16 * (wide ? 4 : 16)), dim3(wide ? 256 : 512), argsT, 0, st);
     }
     void *argsR[] = {&part, &groups, &stride, (void *)&N, (void *)&N1, (void *)&N2, &ia, &ib, &outp};
     return launch(p, 2, spectra, p->kernelR, dim3((N + 31) / 32), dim3(32, 8), argsR, 0, st);
@@ -697,9 +701,7 @@ vspec_status build_plan(vspec_plan *p) {
         p->TB = 256;
         p->smemB = 2 * (size_t)kRow2048Stride * elem;
         p->formB = "row2048";
-        // (with N2 = 16 its 64 CTAs are too few for the 21 slots: the
-        // channel-order fold is faster there)
-        p->fold2048 = N2 >= 64 && !p->kahan;
+        p->fold2048 = N2 >= 16 && !p->kahan;
     }
 
     VSPEC_CUDA(cudaGetDevice(&p->device));

@@ -1295,45 +1295,59 @@ __global__ void __launch_bounds__(256) fold_slots_kernel(void *partial, void *pa
 // The same fold for 2048-point rows (row passes radix 16, 16, 8), N2 >= 16,
 // through a shared-memory tile so that both the slot reads and the
 // accumulator writes are coalesced. Row position posB = 128 q1 + 8 q2 + q3
-// holds k1 = q1 + 16 q2 + 256 q3, so the 32 positions 128 q1 + 32 g .. + 31
-// (q2 = 4g .. 4g+3, all q3) are contiguous in a slot row and, for each of
-// them, 16 consecutive k2 are 16 consecutive channels. A block takes 16
-// consecutive k2 (16 scattered rows pos = invA[k2]) x those 32 positions:
-// it sums the slots in order into the tile, then adds the tile into d_accum.
-// Grid: 4 N2 blocks of 256 threads.
-template <int NPOL>
-__global__ void __launch_bounds__(256) reduce2048_kernel(const void *partial, int groups, int stride, int N,
+// holds k1 = q1 + 16 q2 + 256 q3, so the PB positions 128 q1 + PB g ..
+// + PB - 1 (PB / 8 values of q2, all q3) are contiguous in a slot row and,
+// for each of them, 16 consecutive k2 are 16 consecutive channels. A block
+// takes 16 consecutive k2 (16 scattered rows pos = invA[k2]) x those PB
+// positions. Lane l of L sums slots l, l + L, ... of each element into its
+// tile; the lanes' tiles are then added in order and the result into
+// d_accum. Grid: N2 / 16 x 16 x (128 / PB) blocks of 16 PB L threads (at
+// most 512: PB = 32 runs two elements per thread); the short form, with more
+// CTAs and lanes, is for small N2 with many slots.
+template <int NPOL, int PB, int L>
+__global__ void __launch_bounds__(512) reduce2048_kernel(const void *partial, int groups, int stride, int N,
                                                          int N2, const int *invA, void *out) {
     using A = typename Elem<NPOL>::Acc;
-    __shared__ A tile[16][33];  // [k2 offset][position offset], one pad column
+    constexpr int Q2G = PB / 8;  // q2 values per block
+    constexpr int E = 16 * PB;   // tile elements
+    __shared__ A tile[L][16][PB + 1];  // [lane][k2 offset][position offset], one pad column
     const int nk = N2 / 16;
     const int k2_0 = 16 * (blockIdx.x % nk);
-    const int q1 = (blockIdx.x / nk) % 16, g4 = blockIdx.x / (nk * 16);
-    const int p0 = 128 * q1 + 32 * g4;
+    const int q1 = (blockIdx.x / nk) % 16, g = blockIdx.x / (nk * 16);
+    const int p0 = 128 * q1 + PB * g;
     const A *pp = reinterpret_cast<const A *>(partial);
-    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-        const int r = e >> 5, j = e & 31;
+    for (int e = threadIdx.x; e < E * L; e += blockDim.x) {
+        const int l = e / E, r = (e % E) / PB, j = e % PB;
         const size_t idx = (size_t)__ldg(invA + k2_0 + r) * 2048 + p0 + j;
         A s;
         if constexpr (NPOL == 2) s = make_float4(0.f, 0.f, 0.f, 0.f);
         else s = 0.f;
-        for (int g = 0; g < groups; g++) {
-            const A v = pp[(size_t)g * stride * N + idx];
+        for (int gs = l; gs < groups; gs += L) {
+            const A v = pp[(size_t)gs * stride * N + idx];
             if constexpr (NPOL == 2) {
                 s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
             } else {
                 s += v;
             }
         }
-        tile[r][j] = s;
+        tile[l][r][j] = s;
     }
     __syncthreads();
     A *o = reinterpret_cast<A *>(out);
-    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-        const int r = e & 15, j = e >> 4;  // position offset j = 8 (q2 - 4 g4) + q3
-        const int k1 = q1 + 16 * (4 * g4 + (j >> 3)) + 256 * (j & 7);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int r = e & 15, j = e >> 4;  // position offset j = 8 (q2 - Q2G g) + q3
+        const int k1 = q1 + 16 * (Q2G * g + (j >> 3)) + 256 * (j & 7);
         const size_t k = (size_t)k1 * N2 + k2_0 + r;
-        const A v = tile[r][j];
+        A v = tile[0][r][j];
+#pragma unroll
+        for (int l = 1; l < L; l++) {
+            const A w = tile[l][r][j];
+            if constexpr (NPOL == 2) {
+                v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+            } else {
+                v += w;
+            }
+        }
         if constexpr (NPOL == 2) {
             const float4 a = o[k];
             o[k] = make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w);
