@@ -602,8 +602,10 @@ vspec_status build_plan(vspec_plan *p) {
     p->TA = TA;
     p->kernelA = p->gather ? (p->npol == 2 ? pick_kernel_gather<2>(PPT) : pick_kernel_gather<1>(PPT))
                            : (p->npol == 2 ? pick_kernel_a<2>(PT, PPT) : pick_kernel_a<1>(PT, PPT));
-    if (coldir) p->kernelA = coldir;
-    if (coldir) p->formA = "coldir";
+    if (coldir) {
+        p->kernelA = coldir;
+        p->formA = "coldir";
+    }
     if (p->gather) p->formA = "gather";
     if (!p->kernelA) {
         g_last_error = "no kernel instance for this tap count and size";
