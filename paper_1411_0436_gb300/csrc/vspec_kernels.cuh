@@ -434,9 +434,14 @@ struct ColReg {
     static constexpr int PADG = !kOnePass && C < 8 ? C * R2 : 0, PADW = C;
     static constexpr int SS = PTS + (PADG ? PTS / PADG * PADW : 0);
     __device__ static constexpr int pad(int i) { return PADG ? i + i / PADG * PADW : i; }
-    // data [SPB][SS] P2, twiddle tile [N2][C] float2, raw frames [2][SPB][PTS]
-    // u32, coefficients [PT][PTS] float, first-pass twiddles [TWC] float2
-    static constexpr size_t smem = (size_t)SPB * SS * 16 + (size_t)PTS * 8 + 2 * (size_t)SPB * PTS * 4 +
+    // The twiddle tile likewise: a 16-lane phase of the second pass reads
+    // 16 / C blocks b, R2 rows apart; C pad entries after every R2 rows.
+    static constexpr int TWPAD = !kOnePass && C < 16 ? C : 0;
+    static constexpr int TWS = PTS + (TWPAD ? R1 * TWPAD : 0);
+    __device__ static constexpr int twi(int pos, int c) { return pos * C + c + (TWPAD ? pos / R2 * TWPAD : 0); }
+    // data [SPB][SS] P2, twiddle tile [N2][C] float2 (TWS entries), raw frames
+    // [2][SPB][PTS] u32, coefficients [PT][PTS] float, first-pass twiddles [TWC] float2
+    static constexpr size_t smem = (size_t)SPB * SS * 16 + (size_t)TWS * 8 + 2 * (size_t)SPB * PTS * 4 +
                                    (size_t)PT * PTS * 4 + (size_t)TWC * 8;
     static_assert(smem <= 232448, "shared memory of one CTA");
     static_assert(kOnePass ? N2 <= 16 : (R1 == 8 && (N2 == 32 || N2 == 64 || N2 == 128)), "column shapes of this kernel");
@@ -450,8 +455,8 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int SS = G::SS;
     P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][SS]
-    float2 *tws = reinterpret_cast<float2 *>(data + SPB * SS);         // [N2][C]
-    uint32_t *raw = reinterpret_cast<uint32_t *>(tws + PTS);           // [2][SPB][PTS]
+    float2 *tws = reinterpret_cast<float2 *>(data + SPB * SS);         // [N2][C], at twi(pos, c)
+    uint32_t *raw = reinterpret_cast<uint32_t *>(tws + G::TWS);        // [2][SPB][PTS]
     float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);       // [PT][PTS]
     float2 *twc = reinterpret_cast<float2 *>(cfs + PT * PTS);          // [N2/R1][R1-1]
     const int t = threadIdx.x;                                         // point n2 * C + c
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
         f = base + s_end;
         const int n1_0 = x * C;
         for (int e = t; e < PTS; e += blockDim.x)  // W_N^(n1 k2), k2 = pos
-            tws[e] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
+            tws[G::twi(e / C, e % C)] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
 
         const long long n_pt = n1_0 + (t % C) + (long long)p.N1 * (t / C);
         // the tile's coefficients, read back for every batch so that their
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
                         z[0] = v[0];
 #pragma unroll
-                        for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
+                        for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(q, c)]);
                     }
                 }
             } else {
@@ -576,7 +581,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
 #pragma unroll
-                        for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[(b * R2 + q) * C + c]);
+                        for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(b * R2 + q, c)]);
                     }
                 }
             }
