@@ -3,15 +3,17 @@
 // The N-point DFT of every spectrum is split as N = N1 * N2 (four-step):
 //   n = n1 + N1*n2,  k = k2 + N2*k1,
 //   X[k2 + N2 k1] = sum_n1 W_N1^(n1 k1) [ W_N^(n1 k2) sum_n2 y[n1 + N1 n2] W_N2^(n2 k2) ].
-// Kernel A (fir_colfft) owns a block of C consecutive columns n1 and all N2
-// rows across a run of spectra. Each thread keeps the last P frames of its
-// samples in registers as fp32, so every input byte is read from memory once
-// per run. It applies the pre-filter (§4, PFB), runs the column DFTs over n2
-// in shared memory, multiplies by W_N^(n1 k2) and writes the chunk scratch Z
-// (sized to stay in L2). Kernel B (rowfft_detect) owns rows k2 and runs the
-// row DFTs over n1, fused with detection (§4: X^2, Y^2, Re XY*, Im XY*) and
-// accumulation in shared memory (§4, accumulate). A last small kernel adds
-// the per-group partial sums into the caller's accumulator in channel order.
+// Kernel A (fir_colfft, or its register-column forms fir_colreg and
+// fir_coldir) owns a tile of C consecutive columns n1 and all N2 rows across
+// a run of spectra. Each thread keeps the last P frames of its samples in
+// registers as fp32, so every input byte is read from memory once per run.
+// It applies the pre-filter (§4, PFB), runs the column DFTs over n2 (in
+// registers, or in passes through shared memory), multiplies by
+// W_N^(n1 k2) and writes the chunk scratch Z. Kernel B (row2048 or the
+// general rowfft_detect) owns rows k2 and runs the row DFTs over n1, fused
+// with detection (§4: X^2, Y^2, Re XY*, Im XY*) and accumulation in
+// registers or shared memory (§4, accumulate). A last small kernel adds the
+// per-CTA partial sums into the caller's accumulator in channel order.
 //
 // Both kernels use in-place decimation-in-frequency passes: a pass of radix r
 // over blocks of length lb reads v[q] = x[j + q*m] (m = lb / r), computes the
