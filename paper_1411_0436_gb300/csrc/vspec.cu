@@ -1106,8 +1106,9 @@ static vspec_status run_fused(vspec_plan *p, const int8_t *d_in, int nspectra, f
 }
 
 // Two-kernel path: chunks of column passes (kernel A) and row passes with
-// detection (kernel B) through the L2-resident scratch, then the fold of the
-// partial sums into d_accum, after `before_fold` if it is given.
+// detection (kernel B) through the chunk scratch (in L2 only if a tuned
+// chunk is short enough), then the fold of the partial sums into d_accum,
+// after `before_fold` if it is given.
 static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
                                    cudaStream_t st, cudaEvent_t before_fold) {
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);

@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(512) fir_colfft_kernel(const __grid_constant__
 
 // Kernel A, register-column form: dual-pol PFB of at most 8 taps in tiles of
 // 512 points (one per thread) with columns of N2 = 2 .. 128 points (nchan
-// 2^12 .. 2^18 with 2048-point rows). The FIR stage is the same register
+// 2^12 .. 2^18 with 2048-point rows, 2^19 with 4096-point rows). The FIR
+// stage is the same register
 // window as above. Columns of at most 16 points (R1 == N2) are then whole
 // length-N2 DFTs in registers, one column per thread, in natural output
 // order (the plan's column pass list is the single radix-N2 pass, so
