@@ -1,8 +1,9 @@
 """Benchmark of the GB300 channelizer (arXiv 1411.0436 hot path).
 
 One step = one vspec_execute over one dump of the workload: dual-pol PFB,
-32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra of seeded synthetic
-int8 input resident in HBM. The metric is the real-time dual-polarisation
+131072 channels, 8 taps, Hann-windowed sinc, 4096 spectra of seeded synthetic
+int8 input resident in HBM (2.15 GB; the largest single-GPU workload, the
+precision-stress one on which the tensor-core and FP32 forms are compared). The metric is the real-time dual-polarisation
 bandwidth, S * N / t in GHz (complex sampling: one complex sample per
 polarisation per second of time is one hertz of bandwidth).
 
@@ -22,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -32,7 +34,7 @@ sys.path.insert(0, ROOT)
 from paper_1411_0436_gb300 import workloads  # noqa: E402
 
 METRIC = "Dual-pol real-time bandwidth (GHz) & % HBM roofline, TC-FP16 vs FP32 FFT"
-CONFIG_NAME = "c2"
+CONFIG_NAME = "c4"
 WORKLOADS = {
     "c1": "single-pol PFB, 1024 channels, 8 taps, Hann-windowed sinc, 64 spectra, tone at bin 123.4",
     "c2": ("dual-pol PFB, 32768 channels, 8 taps, Hann-windowed sinc, 1000 spectra per dump, "
@@ -41,7 +43,7 @@ WORKLOADS = {
     "c4": ("dual-pol PFB, 131072 channels, 8 taps, Hann-windowed sinc, 4096 spectra per dump, "
            "sigma=4 with a tone 40 dB above the per-channel noise floor"),
 }
-WORKLOAD = WORKLOADS["c2"]
+WORKLOAD = WORKLOADS[CONFIG_NAME]
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 SM_MAX_MHZ = 2070  # maximum SM clock of the GB300
@@ -113,12 +115,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"vspec_clocks_gpu{self.gpu}_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
@@ -136,20 +138,23 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        lines = []
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
+            lines = f.readlines()
+        os.unlink(self.path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
@@ -423,7 +428,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         variants = {}
         vsteps = max(3, min(args.steps, 50))
         from paper_1411_0436_gb300.vspec import NEVER
-        cands = [("tensor_core_bf16_hilo", PLAN_TENSOR, None), ("fp32_two_kernel", PLAN_TWO_KERNEL, None)]
+        from paper_1411_0436_gb300.vspec import PLAN_KAHAN
+        cands = [("tensor_core_bf16_hilo", PLAN_TENSOR, None), ("fp32_two_kernel", PLAN_TWO_KERNEL, None),
+                 ("fp32_kahan", PLAN_KAHAN, None)]
         if n <= 32768:  # the one-pass cluster kernel on every call length
             cands.append(("fp32_fused_cluster", 0, {"two_kernel_from": NEVER, "assist_permille": 0}))
         for key, flags, tuning in cands:
@@ -489,15 +496,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             v["max_err_norm_rms"] = float(np.max(np.abs(v["out"] - ref) / scale))
         if cufft:
             cufft["max_err_norm_rms"] = float(np.max(np.abs(cout.reshape(n, -1) - ref) / scale))
-        # the FP32 criterion: |G - O| <= 1e-5 * scale + 64 * 2^-24 * own value
-        # (the second term is FP32 rounding of a channel far above the RMS)
+        # the FP32 criterion: |G - O| <= 1e-5 * scale + r(N) * own value, with
+        # r(N) = (log2(N) / 4 + 2) * 2^-24: FP32 rounding of the transform
+        # (a quarter unit per radix-2 level), detection, summation and the
+        # stored result, which bind channels far above the RMS (tones)
         own = np.abs(ref) if bank.npol == 1 else np.concatenate(
             [np.abs(ref[:, :2]), np.repeat(np.sqrt(np.abs(ref[:, :1] * ref[:, 1:2])), 2, axis=1)], axis=1)
-        allowed = 1e-5 * scale + 64 * 2.0 ** -24 * own
+        rtol = (np.log2(n) / 4 + 2) * 2.0 ** -24
+        allowed = 1e-5 * scale + rtol * own
         parity = {"max_err_norm_rms": float(np.max(np.abs(ours_out - ref) / scale)),
                   "tolerance_use": float(np.max(np.abs(ours_out - ref) / allowed)),
                   "against": "FP64 CPU oracle, whole dump",
-                  "criterion": "|G-O| <= 1e-5*RMS + 64*2^-24*|O| per channel (tolerance_use <= 1)"}
+                  "criterion": "|G-O| <= 1e-5*RMS + (log2(N)/4 + 2)*2^-24*|O| per channel (tolerance_use <= 1)"}
+        for v in (variants or {}).values():
+            v["tolerance_use"] = float(np.max(np.abs(v["out"] - ref) / allowed))
     if variants:
         for v in variants.values():
             v.pop("out", None)
@@ -525,8 +537,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                              "frac": alu_achieved / alu_peak, "kernel": name,
                              "flop_per_complex_sample": flop_per_sample,
                              "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ} MHz"},
-            "path_roofline": {"achieved": path_bytes / (total_ms * 1e-3) / 1e9 / world * world,
-                              "frac": path_bytes / (total_ms * 1e-3) / 1e9 / peak},
+            "path_roofline": {"bound": "hbm", "achieved": path_bytes / (total_ms * 1e-3) / 1e9,
+                              "peak": peak, "unit": "GB/s",
+                              "frac": path_bytes / (total_ms * 1e-3) / 1e9 / peak,
+                              "what": "whole path: algorithmic bytes of every step over the mean step time"},
+            "path_alu_roofline": {"bound": "alu",
+                                  "achieved": args.steps * S * flop_per_spec / (total_ms * 1e-3) / 1e12,
+                                  "peak": alu_peak, "unit": "TFLOP/s",
+                                  "frac": args.steps * S * flop_per_spec / (total_ms * 1e-3) / 1e12 / alu_peak,
+                                  "what": "whole path: the method's FP32 flops over the mean step time"},
             "kernels": kernels,
             "plan": plan_desc,
             "gpu_launches": gpu_launches,
@@ -666,8 +685,8 @@ def main():
                     help="bandwidth against FFT length and accumulation length (Fig. 3 shape)")
     ap.add_argument("--spectra", type=int, default=0,
                     help="channelize only the first SPECTRA spectra of the dump (smaller profiling captures)")
-    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
-                    help="c2: the 32768-channel PFB dump (default); c1, c3, c4: the other single-bank "
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default=CONFIG_NAME,
+                    help="c4: the 131072-channel PFB dump (default); c1, c2, c3: the other single-bank "
                          "workloads; c5: the batched multi-beam workload")
     args = ap.parse_args()
     if args.warmup < 3:

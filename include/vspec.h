@@ -126,6 +126,29 @@ VSPEC_API vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int nta
  */
 VSPEC_API vspec_status vspec_plan_check(vspec_plan *plan);
 
+/*
+ * Failure-path controls, for testing how callers handle a device-side wait
+ * that gives up (no GPU fault is involved in either).
+ *
+ * vspec_set_wait_limit sets, for every later launch in the process, how many
+ * times a kernel polls before a bounded wait for its results gives up and
+ * raises the plan's timeout flag (reported by vspec_plan_check or as
+ * VSPEC_ERR_DEVICE_TIMEOUT by vspec_tc_dft16): polls >= 0 sets the limit (0
+ * gives up at once), polls < 0 restores the default of 2^24. The wait that
+ * drains outstanding tensor-core work before a kernel frees its tensor
+ * memory always keeps the default bound. Results computed under a wait that
+ * gave up are incomplete and must be discarded.
+ * Errors: VSPEC_ERR_INVALID_ARG (polls above 2^32 - 1).
+ *
+ * vspec_plan_inject_timeout raises the plan's timeout flag from the host, as
+ * if a device-side wait had expired; the next vspec_plan_check reports
+ * VSPEC_ERR_DEVICE_TIMEOUT and clears it. Synchronous.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_UNSUPPORTED (a plan without
+ * bounded device-side waits), VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_set_wait_limit(long long polls);
+VSPEC_API vspec_status vspec_plan_inject_timeout(vspec_plan *plan);
+
 /* Release a plan and all device memory it owns. NULL is accepted. The caller
  * must make sure no work using the plan is still running on any stream. */
 VSPEC_API vspec_status vspec_plan_destroy(vspec_plan *plan);
@@ -320,20 +343,24 @@ VSPEC_API vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tunin
  * capture loop in which an allocation (which can synchronise the whole
  * device) would stall the data path and drop samples.
  *
- * It computes exactly what a plan created with the same (nchan, ntaps, npol,
- * mode, window) computes in vspec_execute, accumulating into d_accum with the
- * same input and output layouts, but allocates nothing: coefficients,
- * twiddles, chunk scratch and partial sums live in one fixed 20 MiB device
- * array inside this library, which every GPU that loads the library holds
- * until the process exits. Limits: nchan <= 32768 (larger sizes return
- * VSPEC_ERR_UNSUPPORTED with the reason in vspec_last_error); all other
- * arguments and errors are as for vspec_plan_create and vspec_execute.
+ * It channelizes the same problem as a plan created with the same (nchan,
+ * ntaps, npol, mode, window), accumulating into d_accum with the same input
+ * and output layouts, and gives the same result as vspec_execute within the
+ * FP32 tolerance (not bit for bit: it always runs the generic two-kernel form
+ * of the path, in short chunks, where a plan picks faster kernel forms). It
+ * allocates nothing: coefficients, twiddles, chunk scratch and partial sums
+ * live in one fixed 20 MiB device array inside this library, which every GPU
+ * that loads the library holds until the process exits. Limits: nchan <=
+ * 32768 (larger sizes return VSPEC_ERR_UNSUPPORTED with the reason in
+ * vspec_last_error); all other arguments and errors are as for
+ * vspec_plan_create and vspec_execute.
  *
  * The first call on a device (with that device current) looks up the
  * array's device address and sets kernel attributes; make that first call
  * before any stream capture. A call whose (nchan, ntaps, npol, mode, window)
  * differs from the previous call on that device rebuilds the tables in the
- * array on `stream`. Every call shares the array, which keeps the last
+ * array on `stream`; such a call made while `stream` is being captured
+ * returns VSPEC_ERR_UNSUPPORTED (the rebuild would only run at graph launch). Every call shares the array, which keeps the last
  * call's contents, so calls that overlap on the GPU race: serialise them
  * (one stream, or synchronise between calls). Host threads are serialised by
  * an internal lock.

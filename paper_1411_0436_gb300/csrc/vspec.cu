@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdint>
 #include <cstdio>
@@ -28,6 +29,9 @@ using vspec::Pass;
 namespace {
 
 thread_local std::string g_last_error;
+
+// Polls of the bounded device-side waits for results (vspec_set_wait_limit).
+std::atomic<uint32_t> g_wait_limit{vspec::tc::kSpinLimit};
 
 vspec_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -701,7 +705,8 @@ vspec_status build_plan(vspec_plan *p) {
             p->kernelB = k ? (f ? (const void *)row2048_kernel<1, true, true> : (const void *)row2048_kernel<1, true, false>)
                            : (f ? (const void *)row2048_kernel<1, false, true> : (const void *)row2048_kernel<1, false, false>);
         p->TB = 256;
-        p->smemB = 2 * (size_t)kRow2048Stride * elem;
+        // two rows, then (uncompensated plans) the per-thread second-level sums
+        p->smemB = 2 * (size_t)kRow2048Stride * elem + (k ? 0 : (size_t)8 * 256 * accel);
         p->formB = "row2048";
         p->fold2048 = N2 >= 16 && !p->kahan;
     }
@@ -1183,7 +1188,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
         vspec_status r;
         cb.s0 = s0;
         cb.sc = sc;
-        vspec::TcStatus ts{p->tc_status};
+        vspec::TcStatus ts{p->tc_status, g_wait_limit.load()};
         void *argsB[] = {&cb, &ts};
         const int gb = (int)std::min<long long>(nB, (long long)cb.tiles * sc);
         r = launch(p, 1, sc, p->kernelB, dim3(gb), dim3(p->TB), argsB, p->smemB, st);
@@ -1360,6 +1365,23 @@ vspec_status vspec_plan_check(vspec_plan *plan) {
     return VSPEC_ERR_DEVICE_TIMEOUT;
 }
 
+vspec_status vspec_set_wait_limit(long long polls) {
+    if (polls > (long long)UINT32_MAX) return VSPEC_ERR_INVALID_ARG;
+    g_wait_limit.store(polls < 0 ? vspec::tc::kSpinLimit : (uint32_t)polls);
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_inject_timeout(vspec_plan *plan) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (!plan->tc_status) {
+        g_last_error = "this plan has no bounded device-side wait";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    const int one = 1;
+    VSPEC_CUDA(cudaMemcpy(plan->tc_status, &one, sizeof(int), cudaMemcpyHostToDevice));
+    return VSPEC_OK;
+}
+
 vspec_status vspec_tc_dft16(const float *d_x, float *d_y, int batch, int terms, void *stream) {
     if (!d_x || !d_y || batch < 0 || (terms != 1 && terms != 3)) return VSPEC_ERR_INVALID_ARG;
     if (!aligned16(d_x) || !aligned16(d_y)) return VSPEC_ERR_ALIGNMENT;
@@ -1369,7 +1391,8 @@ vspec_status vspec_tc_dft16(const float *d_x, float *d_y, int batch, int terms, 
     cudaStream_t st = (cudaStream_t)stream;
     VSPEC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
     vspec::tc::dft16_kernel<<<(batch + 127) / 128, 128, 0, st>>>(
-        reinterpret_cast<const float2 *>(d_x), reinterpret_cast<float2 *>(d_y), batch, terms, d_status);
+        reinterpret_cast<const float2 *>(d_x), reinterpret_cast<float2 *>(d_y), batch, terms, d_status,
+        g_wait_limit.load());
     VSPEC_CUDA(cudaGetLastError());
     int h = 0;
     VSPEC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1392,10 +1415,11 @@ vspec_status vspec_dump(vspec_plan *plan, float *d_accum, float *h_out, void *st
 
 // ===================================================== allocation-free path ===
 //
-// vspec_execute_noalloc runs the same kernels as vspec_execute, but keeps its
-// coefficients, twiddle tables, digit-reversal maps, chunk scratch and
-// partial sums in one fixed device array declared below instead of memory
-// from cudaMalloc. It exists for callers that cannot allocate device memory:
+// vspec_execute_noalloc channelizes like vspec_execute, with the generic
+// two-kernel form of the path (general kernel A, general row kernel B, plain
+// fold), and keeps its coefficients, twiddle tables, digit-reversal maps,
+// chunk scratch and partial sums in one fixed device array declared below
+// instead of memory from cudaMalloc. It exists for callers that cannot allocate device memory:
 // a host application that owns every byte of device memory through its own
 // pool, or a real-time capture loop where a cudaMalloc (which can synchronise
 // the whole device) would stall the data path and drop samples. The paper
@@ -1475,7 +1499,13 @@ __global__ void noalloc_digrev_kernel(int *kA, int *invA, int *invB, int N2, int
     }
 }
 
-// The same size choices as build_plan, restricted to nchan <= 32768.
+// Sizes of the generic two-kernel form for nchan <= 32768: the four-step
+// split of build_plan (rows of at most 2048 points), with narrower column
+// tiles (16 or 32 byte rows, 256-point tiles) and short chunks, so that the
+// scratch fits the fixed array. build_plan's faster kernel forms (register
+// columns, the 2048-point row kernel, the tiled fold, the cluster kernel) are
+// not used here, so results agree with vspec_execute within the FP32
+// tolerance, not bit for bit.
 vspec_status noalloc_configure(NoAllocCfg *c, int num_sms) {
     const int N = c->N;
     const bool pfb = c->mode == VSPEC_PFB;
@@ -1600,9 +1630,19 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     void *Z = d.base + kNaZ;
     void *partial = d.base + kNaPartial;
 
-    // The array keeps the last call's tables; rebuild them when the problem changes.
+    // The array keeps the last call's tables; rebuild them when the problem
+    // changes. A rebuild enqueued into a stream capture would only run when
+    // the graph is launched, while the host record below would claim the
+    // tables are already there: refuse it.
     const int key[5] = {c.N, c.P, c.npol, c.mode, c.window};
     if (!d.tables_valid || std::memcmp(key, d.key, sizeof(key)) != 0) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        VSPEC_CUDA(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone) {
+            g_last_error = "vspec_execute_noalloc: the problem differs from the previous call's, and its "
+                           "tables cannot be rebuilt inside a stream capture";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
         d.tables_valid = false;
         const int N = c.N, Lc = c.P * N;
         vspec::gen_coef_kernel<<<(Lc + 255) / 256, 256, 0, st>>>(coef, N, Lc, mode == VSPEC_PFB ? 1 : 0, window);

@@ -1079,8 +1079,25 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
 // its eight channels' accumulators live in registers. Rows are stored with
 // one pad element every 8 (pad8), which keeps all three passes' accesses
 // free of bank conflicts.
+//
+// Uncompensated plans sum in two levels: the registers take a run of
+// kRow2048Run spectra, then the run's sums are added into a per-thread
+// second-level sum in shared memory and the registers restart from zero.
+// A segment of S spectra then makes runs of kRow2048Run additions and
+// S / kRow2048Run additions of run sums instead of one chain of S additions,
+// which cuts the FP32 summation error of long segments (hundreds of spectra
+// per CTA on the long workloads) by about the square root of the run length
+// at the cost of one shared-memory read-modify-write per channel per run.
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 constexpr int kRow2048Stride = 2048 + 2048 / 8;
+constexpr int kRow2048Run = 16;  // spectra per register run (a multiple of 2)
+__device__ __forceinline__ void add_acc(float4 &a, float4 b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+__device__ __forceinline__ void add_acc(float &a, float b) { a += b; }
 
 template <int NPOL, bool KAHAN, bool FIR>
 __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<NPOL>::T *row, int x,
@@ -1151,6 +1168,7 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
     using A = typename Elem<NPOL>::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw);  // two rows, pad8 layout
+    A *lvl2 = reinterpret_cast<A *>(rows + 2 * kRow2048Stride);  // [8][256] second-level sums (uncompensated)
     const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127;
     T *own = rows + half * kRow2048Stride;
 
@@ -1168,6 +1186,7 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
             if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             else acc[q] = 0.f;
             comp[q] = acc[q];
+            if constexpr (!KAHAN) lvl2[q * 256 + tid] = acc[q];  // each thread owns its own entries
         }
         for (int s = s_beg; s < s_end; s += 2) {
             const bool two = s + 1 < s_end;
@@ -1175,7 +1194,27 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
             __syncthreads();
             row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
             if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
+            if constexpr (!KAHAN) {
+                if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2) {  // end of a register run
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        A t = lvl2[q * 256 + tid];
+                        add_acc(t, acc[q]);
+                        lvl2[q * 256 + tid] = t;
+                        if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        else acc[q] = 0.f;
+                    }
+                }
+            }
             __syncthreads();  // both rows are free for the next pair
+        }
+        if constexpr (!KAHAN) {  // segment total: the second level plus the last, partial run
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                A t = lvl2[q * 256 + tid];
+                add_acc(t, acc[q]);
+                acc[q] = t;
+            }
         }
 
         // flush: thread t holds positions 8t .. 8t+7 of row tile x

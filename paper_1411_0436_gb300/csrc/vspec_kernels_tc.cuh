@@ -15,7 +15,8 @@
 namespace vspec {
 
 struct TcStatus {
-    int *status;  // set to 1 if a bounded wait for the tensor cores gave up
+    int *status;          // set to 1 if a bounded wait for the tensor cores gave up
+    uint32_t wait_limit;  // polls of that wait (the drain before freeing TMEM always has the full bound)
 };
 
 constexpr int kTcN1 = 2048;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
                 mma_commit(&mbar);
             }
             parity = (uint32_t)(k & 1);
-            ok = mbar_wait(&mbar, parity);
+            ok = mbar_wait(&mbar, parity, ts.wait_limit);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (ok && warp < 4) {
                 float d0[32], d1[32];
@@ -162,7 +163,11 @@ __global__ void __launch_bounds__(256, 1) rowfft_detect_tc_kernel(const __grid_c
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        if (!ok) mbar_wait(&mbar, parity);  // an outstanding MMA finishes before its TMEM is freed
+        // the MMAs of the batch whose wait gave up are still outstanding: wait
+        // for that commit with the full bound before freeing their TMEM (one
+        // batch is under a microsecond of tensor-core work, so only a stopped
+        // tensor pipe could outlast the bound)
+        if (!ok) mbar_wait(&mbar, parity);
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64u) : "memory");
     }
 }

@@ -79,10 +79,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(mbar)), "r"(count) : "memory");
 }
 
-// Wait for phase `parity` of the mbarrier; gives up after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier; gives up after `limit` polls (0:
+// gives up at once without polling). Kernels pass the caller's limit to the
+// wait for their results and always the full kSpinLimit to the wait that
+// drains an outstanding MMA before its tensor memory is freed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t limit = kSpinLimit) {
     const uint32_t a = smem_addr(mbar);
-    for (uint32_t it = 0; it < kSpinLimit; it++) {
+    for (uint32_t it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -186,9 +189,11 @@ __device__ __forceinline__ void fill_w16(float2 *w16) {
 
 // Batched 16-point DFTs, y[b][k] = sum_n x[b][n] W_16^(nk), 128 rows per CTA,
 // `terms` = 1 (X_hi F_hi) or 3 (hi/lo split). *status is set to 1 if the
-// bounded wait for the tensor cores gives up.
+// wait for the tensor cores gives up after wait_limit polls; the CTA then
+// still waits (with the full bound) for its MMAs to finish before it frees
+// their tensor memory.
 __global__ void __launch_bounds__(128) dft16_kernel(const float2 *x, float2 *y, int batch, int terms,
-                                                    int *status) {
+                                                    int *status, uint32_t wait_limit) {
     __shared__ __align__(128) unsigned char ops[2 * kAPart + 2 * kBPart];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(128) dft16_kernel(const float2 *x, float2 *y, 
         issue_dft16(tmem, ahi, alo, bhi, blo, terms);
         mma_commit(&mbar);
     }
-    const bool ok = mbar_wait(&mbar, 0);
+    const bool ok = mbar_wait(&mbar, 0, wait_limit);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         float d[32];

@@ -108,6 +108,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_bank_tuning.restype = i
         lib.vspec_plan_check.argtypes = [vp]
         lib.vspec_plan_check.restype = i
+        lib.vspec_set_wait_limit.argtypes = [ctypes.c_longlong]
+        lib.vspec_set_wait_limit.restype = i
+        lib.vspec_plan_inject_timeout.argtypes = [vp]
+        lib.vspec_plan_inject_timeout.restype = i
         lib.vspec_tc_dft16.argtypes = [vp, vp, i, i, vp]
         lib.vspec_tc_dft16.restype = i
         lib.vspec_execute_host.argtypes = [vp, vp, i, vp, vp]
@@ -284,6 +288,19 @@ def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, wi
         raise VspecError(st, "vspec_execute_noalloc")
 
 
+def vspec_set_wait_limit(polls: int) -> None:
+    """Polls of the bounded device waits for results (< 0: the default)."""
+    st = load().vspec_set_wait_limit(int(polls))
+    if st != OK:
+        raise VspecError(st, "vspec_set_wait_limit")
+
+
+def vspec_plan_inject_timeout(plan: int) -> None:
+    st = load().vspec_plan_inject_timeout(plan)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_inject_timeout")
+
+
 def vspec_tc_dft16(d_x, d_y, batch: int, terms: int = 3, stream=None) -> None:
     st = load().vspec_tc_dft16(_addr(d_x), _addr(d_y), batch, terms, _stream(stream))
     if st != OK:
@@ -341,6 +358,10 @@ class Plan:
     def describe(self) -> str:
         """The plan's decomposition and kernel forms (vspec_plan_describe)."""
         return vspec_plan_describe(self.handle)
+
+    def inject_timeout(self) -> None:
+        """Raise the plan's timeout flag from the host (failure-path tests)."""
+        vspec_plan_inject_timeout(self.handle)
 
     def check(self) -> None:
         """Raise if a bounded device-side wait of this plan expired."""

@@ -72,3 +72,11 @@ def test_describe_rejects_null_arguments(lib):
     import ctypes
     buf = ctypes.create_string_buffer(8)
     assert lib.vspec_plan_describe(None, buf, 8) == vspec.ERR_INVALID_ARG
+
+
+def test_wait_limit_arguments(lib):
+    """Out-of-range wait limits are refused before any CUDA call; a negative
+    value restores the default."""
+    assert lib.vspec_set_wait_limit(ctypes.c_longlong(1 << 33)) == vspec.ERR_INVALID_ARG
+    assert lib.vspec_set_wait_limit(ctypes.c_longlong(-1)) == vspec.OK
+    assert lib.vspec_plan_inject_timeout(None) == vspec.ERR_INVALID_ARG

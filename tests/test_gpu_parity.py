@@ -8,7 +8,7 @@ tails; the full workload sizes are in test_gpu_workloads.py.
 import numpy as np
 import pytest
 
-from parity_util import RTOL_FP32, assert_close
+from parity_util import U32, assert_close
 from paper_1411_0436_gb300 import workloads
 from paper_1411_0436_gb300.workloads import DIRECT, PFB, WIN_HAMMING, WIN_HANN, WIN_RECT, Bank, Tone
 
@@ -155,7 +155,8 @@ def test_accumulates_and_dump_clears():
         plan.execute(d_in, 0, acc)  # no-op
         torch.cuda.synchronize()
         assert torch.count_nonzero(acc).item() == 0
-    assert np.max(np.abs(twice - 2 * once)) <= RTOL_FP32 * np.max(np.abs(twice))
+    # the second call adds the same partials again: doubling is exact in FP32
+    assert np.max(np.abs(twice - 2 * once)) <= 2 * U32 * np.max(np.abs(twice))
 
 
 def test_repeat_runs_are_bitwise_identical():
@@ -332,14 +333,14 @@ def test_subband_mode_matches_oracle(oracle_mod, cfg):
 def test_tensor_core_plan_matches_oracle(oracle_mod, cfg):
     """First row pass on the tensor cores (bf16 hi/lo): within the tensor-core
     tolerance of the oracle."""
-    from parity_util import ATOL_TC, RTOL_TC, metrics
+    from parity_util import ATOL_TC, metrics
     from paper_1411_0436_gb300.vspec import PLAN_TENSOR, Plan
     n, p, npol, mode, win, s = cfg
     bank = Bank(n, p, npol, mode, win, s, rho=0.3, tones=(Tone(40.0, n * 0.2 + 0.37, (0, 1)),))
     x = workloads.generate(bank, 321 + n)
     o = run_oracle(oracle_mod, bank, x)
     g = run_gpu(bank, x, flags=PLAN_TENSOR)
-    m = assert_close(g, o, atol=ATOL_TC, rtol=RTOL_TC, what=f"{cfg} tensor")
+    m = assert_close(g, o, atol=ATOL_TC, what=f"{cfg} tensor")
     print(f"\n{cfg}: normalised max error {m['pure']:.3e} (fp32 path: "
           f"{metrics(run_gpu(bank, x), o)['pure']:.3e})")
     with Plan(n, p, npol, mode, win, PLAN_TENSOR) as plan:
@@ -360,7 +361,7 @@ def test_tensor_core_plan_rejects_other_sizes():
 def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
     """Kahan accumulation (alone and with the tensor-core pass) stays within
     the tolerances; dump clears the compensation with the accumulator."""
-    from parity_util import ATOL_TC, RTOL_TC, metrics
+    from parity_util import ATOL_TC, metrics
     from paper_1411_0436_gb300.vspec import PLAN_KAHAN, PLAN_TENSOR, Plan
     n, p, npol, mode, win, s = cfg
     bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0,
@@ -371,7 +372,7 @@ def test_compensated_accumulation_matches_oracle(oracle_mod, cfg):
     mp = metrics(run_gpu(bank, x, flags=1), o)
     print(f"\n{cfg}: normalised max error plain {mp['pure']:.3e}, compensated {mk['pure']:.3e}")
     if npol == 2 and 2048 <= n <= 524288:  # the tensor-core pass needs 2048-point rows
-        assert_close(run_gpu(bank, x, flags=PLAN_KAHAN | PLAN_TENSOR), o, atol=ATOL_TC, rtol=RTOL_TC,
+        assert_close(run_gpu(bank, x, flags=PLAN_KAHAN | PLAN_TENSOR), o, atol=ATOL_TC,
                      what=f"{cfg} kahan+tensor")
     with Plan(n, p, npol, mode, win, PLAN_KAHAN) as plan:  # twice, dump in between
         d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
