@@ -705,8 +705,7 @@ vspec_status build_plan(vspec_plan *p) {
             p->kernelB = k ? (f ? (const void *)row2048_kernel<1, true, true> : (const void *)row2048_kernel<1, true, false>)
                            : (f ? (const void *)row2048_kernel<1, false, true> : (const void *)row2048_kernel<1, false, false>);
         p->TB = 256;
-        // two rows, then (uncompensated plans) the per-thread second-level sums
-        p->smemB = 2 * (size_t)kRow2048Stride * elem + (k ? 0 : (size_t)8 * 256 * accel);
+        p->smemB = 2 * (size_t)kRow2048Stride * elem;
         p->formB = "row2048";
         p->fold2048 = N2 >= 16 && !p->kahan;
     }

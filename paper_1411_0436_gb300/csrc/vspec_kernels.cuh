@@ -896,6 +896,8 @@ __device__ __forceinline__ typename Elem<NPOL>::T fir_ring(const unsigned char *
     else return make_float2(a[0], a[1]);
 }
 
+constexpr int kRowRun = 16;  // spectra per accumulator run of the general row kernel
+
 template <int R, int NPOL, bool KAHAN = false, bool FIR = false>
 __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typename Elem<NPOL>::T *data,
                                               typename Elem<NPOL>::Acc *acc,
@@ -1001,6 +1003,31 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
             else acc[e] = 0.f;
             if constexpr (KAHAN) comp[e] = acc[e];
         }
+        // add the accumulators into this block's slot: accumulator e = q * U +
+        // (r * N1/R + b) holds row r, position b*R + q; `store`: the slot's
+        // first write this call. Each thread flushes the entries it zeroes.
+        auto flush = [&](bool store) {
+            const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N;
+            A *part = reinterpret_cast<A *>(p.partial) + so;
+            for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+                const int q = e >> lU, w = e & ((1 << lU) - 1);
+                const int r = w >> lq, b = w & ((1 << lq) - 1);
+                const size_t o = (size_t)(x * p.RB + r) * p.N1 + b * RL + q;
+                if constexpr (KAHAN) {
+                    A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
+                    A a = part[o], c = pc[o];
+                    if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[e], comp[e]));
+                    else kahan_add(a, c, acc[e] - comp[e]);
+                    part[o] = a;
+                    pc[o] = c;
+                } else if (store) {
+                    part[o] = acc[e];
+                } else {
+                    atomicAdd(part + o, acc[e]);  // in L2, one writer per entry (see row2048_kernel)
+                }
+            }
+        };
+        bool first = p.store != 0;
         if constexpr (FIR) {  // the segment's first spectrum's P frames
             for (int t = 0; t < p.P; t++) stage_frame(p.s0 + s_beg + t);
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -1039,33 +1066,25 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
                 }
                 __syncthreads();
             }
-        }
-
-        // flush into this block's slot: accumulator slot e = q * U + (r * N1/R + b)
-        // holds row r, position b*R + q
-        const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N;
-        A *part = reinterpret_cast<A *>(p.partial) + so;
-        for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
-            const int q = e >> lU, w = e & ((1 << lU) - 1);
-            const int r = w >> lq, b = w & ((1 << lq) - 1);
-            const size_t o = (size_t)(x * p.RB + r) * p.N1 + b * RL + q;
-            if constexpr (KAHAN) {
-                A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
-                A a = part[o], c = pc[o];
-                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[e], comp[e]));
-                else kahan_add(a, c, acc[e] - comp[e]);
-                part[o] = a;
-                pc[o] = c;
-            } else if (p.store) {
-                part[o] = acc[e];
-            } else if constexpr (NPOL == 2) {
-                float4 a = part[o];
-                const float4 d = acc[e];
-                part[o] = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
-            } else {
-                part[o] += acc[e];
+            // uncompensated sums: after a run of kRowRun spectra with more to
+            // come, into the slot (two-level summation, as in the 2048-point
+            // kernel); the barrier orders the zeroing before the next
+            // spectrum's last pass adds again (a one-pass row adds in its
+            // first pass)
+            if constexpr (!KAHAN) {
+                if ((s - s_beg) % kRowRun == kRowRun - 1 && s + 1 < s_end) {
+                    flush(first);
+                    first = false;
+                    for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+                        if constexpr (NPOL == 2) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        else acc[e] = 0.f;
+                    }
+                    __syncthreads();
+                }
             }
         }
+
+        flush(first);
         __syncthreads();  // acc is zeroed again by the next segment
     }
 }
@@ -1081,23 +1100,16 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
 // free of bank conflicts.
 //
 // Uncompensated plans sum in two levels: the registers take a run of
-// kRow2048Run spectra, then the run's sums are added into a per-thread
-// second-level sum in shared memory and the registers restart from zero.
-// A segment of S spectra then makes runs of kRow2048Run additions and
-// S / kRow2048Run additions of run sums instead of one chain of S additions,
-// which cuts the FP32 summation error of long segments (hundreds of spectra
-// per CTA on the long workloads) by about the square root of the run length
-// at the cost of one shared-memory read-modify-write per channel per run.
+// kRow2048Run spectra, then the run's sums are added into the CTA's
+// partial-sum slot (in L2) and the registers restart from zero. A segment of
+// S spectra then makes runs of kRow2048Run additions and S / kRow2048Run
+// additions of run sums instead of one chain of S additions, which cuts the
+// FP32 summation error of long segments (hundreds of spectra per CTA on the
+// long workloads) by about the square root of the run length, for one
+// reduction into L2 of the thread's eight channels per run.
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 constexpr int kRow2048Stride = 2048 + 2048 / 8;
 constexpr int kRow2048Run = 16;  // spectra per register run (a multiple of 2)
-__device__ __forceinline__ void add_acc(float4 &a, float4 b) {
-    a.x += b.x;
-    a.y += b.y;
-    a.z += b.z;
-    a.w += b.w;
-}
-__device__ __forceinline__ void add_acc(float &a, float b) { a += b; }
 
 template <int NPOL, bool KAHAN, bool FIR>
 __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<NPOL>::T *row, int x,
@@ -1168,7 +1180,6 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
     using A = typename Elem<NPOL>::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw);  // two rows, pad8 layout
-    A *lvl2 = reinterpret_cast<A *>(rows + 2 * kRow2048Stride);  // [8][256] second-level sums (uncompensated)
     const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127;
     T *own = rows + half * kRow2048Stride;
 
@@ -1186,8 +1197,32 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
             if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             else acc[q] = 0.f;
             comp[q] = acc[q];
-            if constexpr (!KAHAN) lvl2[q * 256 + tid] = acc[q];  // each thread owns its own entries
         }
+        // add the registers into this block's slot (thread t holds positions
+        // 8t .. 8t+7 of row tile x); `store`: the slot's first write this call
+        auto flush = [&](bool store) {
+            const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
+            A *part = reinterpret_cast<A *>(p.partial) + so;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if constexpr (KAHAN) {
+                    A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
+                    A a = part[q], c = pc[q];
+                    if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
+                    else kahan_add(a, c, acc[q] - comp[q]);
+                    part[q] = a;
+                    pc[q] = c;
+                } else if (store) {
+                    part[q] = acc[q];
+                } else {
+                    // a reduction performed in L2: no wait for the slot's old
+                    // value. Only this thread adds to these entries, in program
+                    // order, so the sums are the same as a load-add-store's.
+                    atomicAdd(part + q, acc[q]);
+                }
+            }
+        };
+        bool first = p.store != 0;
         for (int s = s_beg; s < s_end; s += 2) {
             const bool two = s + 1 < s_end;
             if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR>(p, own, x, s + half, ht, half);
@@ -1195,12 +1230,12 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
             row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
             if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
             if constexpr (!KAHAN) {
-                if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2) {  // end of a register run
+                // end of a register run with more spectra to come: into the slot
+                if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2 && s + 2 < s_end) {
+                    flush(first);
+                    first = false;
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
-                        A t = lvl2[q * 256 + tid];
-                        add_acc(t, acc[q]);
-                        lvl2[q * 256 + tid] = t;
                         if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                         else acc[q] = 0.f;
                     }
@@ -1208,36 +1243,7 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
             }
             __syncthreads();  // both rows are free for the next pair
         }
-        if constexpr (!KAHAN) {  // segment total: the second level plus the last, partial run
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                A t = lvl2[q * 256 + tid];
-                add_acc(t, acc[q]);
-                acc[q] = t;
-            }
-        }
-
-        // flush: thread t holds positions 8t .. 8t+7 of row tile x
-        const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
-        A *part = reinterpret_cast<A *>(p.partial) + so;
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if constexpr (KAHAN) {
-                A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
-                A a = part[q], c = pc[q];
-                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
-                else kahan_add(a, c, acc[q] - comp[q]);
-                part[q] = a;
-                pc[q] = c;
-            } else if (p.store) {
-                part[q] = acc[q];
-            } else if constexpr (NPOL == 2) {
-                const float4 a = part[q];
-                part[q] = make_float4(a.x + acc[q].x, a.y + acc[q].y, a.z + acc[q].z, a.w + acc[q].w);
-            } else {
-                part[q] += acc[q];
-            }
-        }
+        flush(first);
     }
 }
 
