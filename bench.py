@@ -299,7 +299,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     x = workloads.generate(bank, beam_seed(rank, config))
     in_bytes = x.nbytes
     n, S = bank.nchan, bank.nspectra
-    plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window)
+    plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window, args.plan_flags)
     plan_desc = plan.describe()  # decomposition and kernel forms, for the JSON line
     d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).to(dev)
     acc = torch.zeros(plan.out_floats, dtype=torch.float32, device=dev)
@@ -429,8 +429,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         vsteps = max(3, min(args.steps, 50))
         from paper_1411_0436_gb300.vspec import NEVER
         from paper_1411_0436_gb300.vspec import PLAN_KAHAN
-        cands = [("tensor_core_bf16_hilo", PLAN_TENSOR, None), ("fp32_two_kernel", PLAN_TWO_KERNEL, None),
-                 ("fp32_kahan", PLAN_KAHAN, None)]
+        from paper_1411_0436_gb300.vspec import PLAN_TENSOR_INT8
+        cands = [("tensor_core", PLAN_TENSOR, None), ("tensor_core_int8", PLAN_TENSOR_INT8, None),
+                 ("fp32_two_kernel", PLAN_TWO_KERNEL, None), ("fp32_kahan", PLAN_KAHAN, None)]
         if n <= 32768:  # the one-pass cluster kernel on every call length
             cands.append(("fp32_fused_cluster", 0, {"two_kernel_from": NEVER, "assist_permille": 0}))
         for key, flags, tuning in cands:
@@ -510,14 +511,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                   "criterion": "|G-O| <= 1e-5*RMS + (log2(N)/4 + 2)*2^-24*|O| per channel (tolerance_use <= 1)"}
         allowed_tc = 1e-3 * scale + rtol * own  # the tensor-core form's bound: 1e-3 of the RMS
         for v in (variants or {}).values():
-            tc_form = bool(v.get("flags", 0) & 2)
+            tc_form = bool(v.get("flags", 0) & 10)  # VSPEC_PLAN_TENSOR or VSPEC_PLAN_TENSOR_INT8
             v["tolerance_use"] = float(np.max(np.abs(v["out"] - ref) / (allowed_tc if tc_form else allowed)))
             v["tolerance"] = "1e-3*RMS + r(N)*|O|" if tc_form else "1e-5*RMS + r(N)*|O|"
     if variants:
         for v in variants.values():
             v.pop("out", None)
-        variants["tc_speedup_over_fp32"] = (variants["tensor_core_bf16_hilo"]["value"] /
+        variants["tc_speedup_over_fp32"] = (variants["tensor_core"]["value"] /
                                             variants["fp32_default"]["value"])
+        variants["tc_int8_speedup_over_fp32"] = (variants["tensor_core_int8"]["value"] /
+                                                 variants["fp32_default"]["value"])
 
     plan.close()
     if rank == 0:
@@ -686,6 +689,8 @@ def main():
                     help="skip the tensor-core and two-kernel comparison runs")
     ap.add_argument("--sweep", action="store_true",
                     help="bandwidth against FFT length and accumulation length (Fig. 3 shape)")
+    ap.add_argument("--plan-flags", type=int, default=0,
+                    help="VSPEC_PLAN_* flags of the timed plan (profiling other plan forms; 0: the default)")
     ap.add_argument("--spectra", type=int, default=0,
                     help="channelize only the first SPECTRA spectra of the dump (smaller profiling captures)")
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default=CONFIG_NAME,

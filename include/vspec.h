@@ -85,11 +85,24 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
 /* Plan flags for vspec_plan_create_ex. */
 #define VSPEC_PLAN_TWO_KERNEL 1u /* use the general two-kernel path even where the one-pass
                                     fused path applies (for comparison and testing) */
-#define VSPEC_PLAN_TENSOR 2u     /* two-kernel path with the first radix-16 pass of every
-                                    2048-point row on the tensor cores (bf16 hi/lo operands,
-                                    fp32 accumulation, see vspec_tc_dft16); dual-pol only,
-                                    nchan 2^11..2^20 where the rows are 2048 points; other
-                                    sizes return VSPEC_ERR_UNSUPPORTED */
+#define VSPEC_PLAN_TENSOR 2u     /* two-kernel path with DFT stages on the tensor cores;
+                                    dual-pol only, nchan 2^11..2^20 where the rows are 2048
+                                    points (other sizes return VSPEC_ERR_UNSUPPORTED).
+                                    PFB of 5..8 taps at nchan 2^15..2^17: kernel A's whole
+                                    column DFT (16, 32 or 64 points) as one tensor-core
+                                    product of the fp16-rounded FIR output with the DFT
+                                    matrix in fp16 hi/lo parts (two MMA terms), fp32
+                                    accumulation. Other sizes and direct mode: the first
+                                    radix-16 pass of every row with bf16 hi/lo operands
+                                    (about 16 bits, vspec_tc_dft16). */
+#define VSPEC_PLAN_TENSOR_INT8 8u /* two-kernel path whose kernel A is one tensor-core product
+                                    per column on the int8 input itself (exact in fp16): the
+                                    pre-filter taps and the column DFT folded into fp16
+                                    coefficient matrices computed at plan time (high and low
+                                    parts where they fit in shared memory), fp32
+                                    accumulation. Dual-pol PFB of at most 8 taps or direct
+                                    mode, nchan 2^15..2^17 (else VSPEC_ERR_UNSUPPORTED).
+                                    Combinable with VSPEC_PLAN_KAHAN. */
 #define VSPEC_PLAN_KAHAN 4u      /* compensated (Kahan) FP32 accumulation at every level: over
                                     spectra in the kernel, across groups and into the caller's
                                     accumulator through a plan-owned compensation buffer that

@@ -23,6 +23,8 @@
 #include "vspec_kernels.cuh"
 #include "vspec_tc.cuh"
 #include "vspec_kernels_tc.cuh"
+#include "vspec_kernels_coltc.cuh"
+#include "vspec_kernels_tcfir.cuh"
 
 using vspec::Pass;
 
@@ -155,6 +157,10 @@ struct vspec_plan {
     cudaStream_t assist_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_main = nullptr, ev_assist = nullptr;
     bool tc = false;           // first row pass on the tensor cores
+    bool tc_cols = false;      // column DFTs (kernel A) on the tensor cores
+    bool tc_int8 = false;      // ... with the pre-filter, on the int8 input (per-column operands)
+    int bterms = 1;            // their coefficient parts (fp16 hi, or hi and lo)
+    unsigned char *dftop = nullptr;  // their DFT operand (fp16 hi, lo)
     bool kahan = false;        // compensated accumulation at every level
     void *partial_comp = nullptr, *out_comp = nullptr;
     int *tc_status = nullptr;  // bounded-wait flag of the tensor-core kernel
@@ -227,6 +233,36 @@ const void *pick_kernel_coldir(int N2, size_t *smem, std::vector<int> *radices) 
         case 64: *smem = ColDir<64>::smem; return (const void *)fir_coldir_kernel<64>;
         case 128: *smem = ColDir<128>::smem; return (const void *)fir_coldir_kernel<128>;
         case 256: *smem = ColDir<256>::smem; return (const void *)fir_coldir_kernel<256>;
+    }
+    return nullptr;
+}
+
+// kernel A with the column DFTs on the tensor cores (dual-pol PFB, 8 taps,
+// 512-point tiles) for N2 in 16 .. 64; one column pass of radix N2 (natural order)
+const void *pick_kernel_coltc(int N2, size_t *smem) {
+    using namespace vspec;
+    switch (N2) {
+        case 16: *smem = ColTc<16>::smem; return (const void *)fir_coltc_kernel<16>;
+        case 32: *smem = ColTc<32>::smem; return (const void *)fir_coltc_kernel<32>;
+        case 64: *smem = ColTc<64>::smem; return (const void *)fir_coltc_kernel<64>;
+    }
+    return nullptr;
+}
+
+// kernel A as tensor-core products on the int8 input (pre-filter and column
+// DFT together), N2 = 16 Q for Q = 1, 2, 4
+// (terms = 2: high and low fp16 parts of the coefficients where they fit in
+// shared memory, else 1)
+const void *pick_kernel_tcfir(int N2, int P, size_t *smem, int *terms) {
+    using namespace vspec;
+    constexpr size_t cap = 232448 - 1024;
+    switch (N2) {
+        case 16: *terms = TcFir<1>::smem_for(P, 2) <= cap ? 2 : 1; *smem = TcFir<1>::smem_for(P, *terms);
+                 return (const void *)fir_tcfir_kernel<1>;
+        case 32: *terms = TcFir<2>::smem_for(P, 2) <= cap ? 2 : 1; *smem = TcFir<2>::smem_for(P, *terms);
+                 return (const void *)fir_tcfir_kernel<2>;
+        case 64: *terms = TcFir<4>::smem_for(P, 2) <= cap ? 2 : 1; *smem = TcFir<4>::smem_for(P, *terms);
+                 return (const void *)fir_tcfir_kernel<4>;
     }
     return nullptr;
 }
@@ -413,6 +449,7 @@ void free_plan(vspec_plan *p) {
     cudaFree(p->partial);
     cudaFree(p->sb_scratch);
     cudaFree(p->tc_status);
+    cudaFree(p->dftop);
     cudaFree(p->partial_comp);
     cudaFree(p->out_comp);
     delete p;
@@ -547,7 +584,8 @@ vspec_status build_plan(vspec_plan *p) {
     const int N = p->N;
     const int e = ilog2(N);
     const bool pfb = p->mode == VSPEC_PFB;
-    if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN)) && p->npol == 2 && N >= 2048 &&
+    if (!(p->flags & (VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN | VSPEC_PLAN_TENSOR_INT8)) &&
+        p->npol == 2 && N >= 2048 &&
         N <= 32768 && (!pfb || p->P == 8))
         return build_fused_plan(p);
     int PT = p->P <= 1 ? 1 : p->P <= 2 ? 2 : p->P <= 4 ? 4 : p->P <= 8 ? 8 : 16;
@@ -639,8 +677,39 @@ vspec_status build_plan(vspec_plan *p) {
         p->kernelA = colreg;
         p->formA = "colreg";
     }
+    // tensor-core plans with 2048-point rows and N2 = 16, 32, 64:
+    //  - VSPEC_PLAN_TENSOR_INT8 (PFB of at most 8 taps, or direct): pre-filter
+    //    and column DFT as one tensor-core product on the int8 input, one
+    //    column per CTA, groups of 8 CTAs on 8 adjacent columns;
+    //  - VSPEC_PLAN_TENSOR, dual-pol PFB of 5 .. 8 taps: the register-column
+    //    FIR, then the column DFTs as tensor-core products (fp16 Y, split F).
+    size_t smem_tcA = 0;
+    const bool want_int8 = (p->flags & VSPEC_PLAN_TENSOR_INT8) != 0;
+    const void *tcfir = want_int8 && p->npol == 2 && N1 == 2048 && p->P <= 8 && !p->gather
+                            ? pick_kernel_tcfir(N2, p->P, &smem_tcA, &p->bterms) : nullptr;
+    if (want_int8 && !tcfir) {
+        g_last_error = "the int8 tensor-core form needs dual-pol, at most 8 taps and nchan 2^15 .. 2^17";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    const void *coltc = !want_int8 && (p->flags & VSPEC_PLAN_TENSOR) && colreg && N1 == 2048
+                            ? pick_kernel_coltc(N2, &smem_tcA) : nullptr;
+    if (tcfir) {
+        p->kernelA = tcfir;
+        p->formA = "tensor-int8";
+        p->tc_cols = p->tc_int8 = true;
+        p->C = 1;
+        p->tileG = 8;
+        p->TA = 512;
+        p->PPT = 1;
+    }
+    if (coltc) {
+        p->kernelA = coltc;
+        p->formA = "tensor";
+        p->tc_cols = true;
+    }
     if (p->fir_b) p->formA = "none";
-    const std::vector<int> rA = colreg ? r_colreg : coldir ? r_coldir : radix_list(e2, maxbitsA),
+    const std::vector<int> rA = (tcfir || coltc) ? std::vector<int>{N2} : colreg ? r_colreg : coldir ? r_coldir
+                                                                               : radix_list(e2, maxbitsA),
                            rB = radix_list(e1);
     int twA_n = 0, twB_n = 0;
     p->passA = make_passes(N2, rA, &twA_n);
@@ -654,7 +723,7 @@ vspec_status build_plan(vspec_plan *p) {
     int maxb = 1;
     for (const Pass &ps : p->passB) maxb = std::max(maxb, p->RB * (N1 / ps.r));
     p->TB = std::min(256, std::max(32, maxb));
-    if (p->flags & VSPEC_PLAN_TENSOR) {
+    if ((p->flags & VSPEC_PLAN_TENSOR) && !p->tc_cols) {
         if (p->npol != 2 || N1 != vspec::kTcN1 || p->RB != 1 || p->passB[0].r != 16) {
             g_last_error = "tensor-core stage needs dual-pol and 2048-point rows (nchan 2^11 .. 2^20)";
             return VSPEC_ERR_UNSUPPORTED;
@@ -682,6 +751,7 @@ vspec_status build_plan(vspec_plan *p) {
     p->smemA = (size_t)PT * N2 * C * elem + (size_t)N2 * C * sizeof(float2) +
                (!p->gather ? 2 * (size_t)PT * N2 * C * p->npol * 2 : 0);
     if (colreg) p->smemA = smem_colreg;
+    if (tcfir || coltc) p->smemA = smem_tcA;
     if (coldir) p->smemA = smem_coldir;
     p->smemB = (size_t)p->RB * (N1 + (N1 >> 4)) * elem + (size_t)p->RB * N1 * accel;
     if (p->kahan) p->smemB += (size_t)p->RB * N1 * accel;
@@ -698,7 +768,9 @@ vspec_status build_plan(vspec_plan *p) {
         p->passB[1].r == 16 && p->passB[2].r == 8) {
         using namespace vspec;
         const bool k = p->kahan, f = p->fir_b;
-        if (p->npol == 2)
+        if (p->npol == 2 && coltc)  // scratch elements in the tensor-core column kernel's order
+            p->kernelB = k ? (const void *)row2048_kernel<2, true, false, true> : (const void *)row2048_kernel<2, false, false, true>;
+        else if (p->npol == 2)
             p->kernelB = k ? (f ? (const void *)row2048_kernel<2, true, true> : (const void *)row2048_kernel<2, true, false>)
                            : (f ? (const void *)row2048_kernel<2, false, true> : (const void *)row2048_kernel<2, false, false>);
         else
@@ -741,9 +813,15 @@ vspec_status build_plan(vspec_plan *p) {
     p->sc_alloc = p->fir_b ? 0 : p->sc_max;
     if ((st = dev_alloc(&p->Z, (size_t)std::max(1, p->sc_alloc) * N * elem, &tot))) return st;
     if ((st = dev_alloc(&p->partial, (size_t)p->slots_cap * N * accel, &tot))) return st;
-    if (p->tc) {
+    if (p->tc || p->tc_cols) {
         if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
         VSPEC_CUDA(cudaMemset(p->tc_status, 0, sizeof(int)));
+    }
+    if (p->tc_int8) {  // the per-column B blocks: N1 columns x Q residues x P taps x 2 KiB (x terms)
+        if ((st = dev_alloc((void **)&p->dftop, (size_t)N1 * (N2 / 16) * p->P * p->bterms * 2048, &tot)))
+            return st;
+    } else if (p->tc_cols) {  // the column DFT operand F, hi and lo
+        if ((st = dev_alloc((void **)&p->dftop, (size_t)2 * (2 * N2) * (2 * N2) * 2, &tot))) return st;
     }
     if (p->kahan) {
         if ((st = dev_alloc(&p->partial_comp, (size_t)p->slots_cap * N * accel, &tot))) return st;
@@ -773,6 +851,13 @@ vspec_status build_plan(vspec_plan *p) {
             if (ps.m * (ps.r - 1) > 0)
                 vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256, 0, s0>>>(p->twB, ps);
         vspec::gen_twz_kernel<<<(N + 255) / 256, 256, 0, s0>>>(p->twZ, N, N1, N2, d_kA);
+        if (p->tc_cols && !p->tc_int8)
+            vspec::gen_coltc_operand_kernel<<<(4 * N2 * N2 + 255) / 256, 256, 0, s0>>>(p->dftop, N2);
+        if (p->tc_int8) {
+            const long long nb = (long long)N1 * (N2 / 16) * p->P * 1024;
+            vspec::gen_tcfir_operand_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s0>>>(p->dftop, p->coef, N, N1,
+                                                                                      N2 / 16, p->P, p->bterms);
+        }
         ce = cudaGetLastError();
         if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
     }
@@ -875,7 +960,7 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
     p->npol = npol;
     p->mode = mode;
     p->window = window;
-    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN)) {
+    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN | VSPEC_PLAN_TENSOR_INT8)) {
         delete p;
         *out = nullptr;
         return VSPEC_ERR_INVALID_ARG;
@@ -1151,6 +1236,10 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     ca.tiles = p->N1 / p->C;
     ca.G = p->tileG;
     ca.win = p->mode == VSPEC_DIRECT && p->window != VSPEC_WIN_RECT;
+    ca.dftop = p->dftop;
+    ca.status = p->tc_status;
+    ca.wait_limit = g_wait_limit.load();
+    ca.bterms = p->bterms;
 
     vspec::RowParams cb{};
     cb.Z = p->Z;

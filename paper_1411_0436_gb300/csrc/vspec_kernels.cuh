@@ -56,6 +56,11 @@ struct ColParams {
     int tiles;           // column tiles, N1 / C
     int G;               // tiles per group (tile_split); 0 or 1: no groups
     int win;             // direct mode with a window: multiply by coef (register-column kernels)
+    // tensor-core column kernel only
+    const unsigned char *dftop;  // the column DFT operand: fp16 hi part, then lo part
+    int *status;                 // set to 1 if a bounded wait for the tensor cores gave up
+    unsigned wait_limit;         // polls of that wait
+    int bterms;                  // fp16 parts of the fused tensor-core operand: 1 (hi) or 2 (hi, lo)
 };
 
 struct RowParams {
@@ -1111,7 +1116,9 @@ __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 constexpr int kRow2048Stride = 2048 + 2048 / 8;
 constexpr int kRow2048Run = 16;  // spectra per register run (a multiple of 2)
 
-template <int NPOL, bool KAHAN, bool FIR>
+// ZSPLIT: the scratch elements hold (X.re, X.im, Y.re, Y.im) (the tensor-core
+// column kernel's order) instead of the packed (X.re, Y.re, X.im, Y.im).
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
 __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<NPOL>::T *row, int x,
                                               int s, int ht, int half) {
     using T = typename Elem<NPOL>::T;
@@ -1122,6 +1129,13 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<
         if constexpr (FIR) {
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] = fir_sample<NPOL>(p, p.s0 + s, ht + 128 * q);
+        } else if constexpr (ZSPLIT) {
+            const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const float4 e = zr[ht + 128 * q];
+                v[q] = make_p2(e.x, e.y, e.z, e.w);
+            }
         } else {
             const T *zr = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
 #pragma unroll
@@ -1174,7 +1188,7 @@ __device__ __forceinline__ void row2048_last(const typename Elem<NPOL>::T *row, 
     }
 }
 
-template <int NPOL, bool KAHAN, bool FIR>
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
 __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __grid_constant__ RowParams p) {
     using T = typename Elem<NPOL>::T;
     using A = typename Elem<NPOL>::Acc;
@@ -1225,7 +1239,7 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
         bool first = p.store != 0;
         for (int s = s_beg; s < s_end; s += 2) {
             const bool two = s + 1 < s_end;
-            if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR>(p, own, x, s + half, ht, half);
+            if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR, ZSPLIT>(p, own, x, s + half, ht, half);
             __syncthreads();
             row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
             if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);

@@ -1,0 +1,333 @@
+// vspec_kernels_coltc.cuh — kernel A with the column DFTs on the tensor cores.
+//
+// Same work as fir_colreg_kernel (§4: pre-filter, then the length-N2 column
+// DFTs of the four-step FFT, times W_N^(n1 k2), into the chunk scratch), for
+// dual-pol PFB plans of 5 to 8 taps with N2 = 16, 32 or 64 (512-point column
+// tiles, C = 512 / N2 columns). The FIR runs on the CUDA cores from the same
+// register window as fir_colreg_kernel. The column DFTs of a batch of SPB
+// spectra are then one dense real matrix product per 128 rows:
+//
+//   D (rows x 2 N2) = Y (rows x 2 N2) . F (2 N2 x 2 N2),
+//   row = (spectrum u, polarisation p, column c) = (2 u + p) C + c,
+//   K index 2 n2 + {0: re, 1: im},  N index 2 k2 + {0: re, 1: im},
+//   F[2n2][2k2] = cos, F[2n2][2k2+1] = -sin, F[2n2+1][2k2] = sin,
+//   F[2n2+1][2k2+1] = cos  of 2 pi n2 k2 / N2,
+//
+// so D's row holds sum_n2 y[n1 + N1 n2] W_N2^(n2 k2) in natural k2 order
+// (times a power of two, kColTc*, that keeps the fp16 low parts normal). D
+// has two buffers in tensor memory, each as two accumulators (the two halves
+// of the K slices, added in FP32 by the epilogue): the epilogue of one batch
+// runs while the tensor cores compute the next.
+// Y and F are split into fp16 high and low parts (x = hi + lo, hi =
+// fp16(x), lo = fp16(x - hi)) and three tcgen05.mma terms, Y_hi F_hi +
+// Y_lo F_hi + Y_hi F_lo, accumulate in FP32 in tensor memory: about 22
+// significant bits of each operand (the dropped Y_lo F_lo is below 2^-22).
+// Both low parts matter: an emulation of this stage with Y rounded to fp16
+// alone gives 9e-4 of the spectrum RMS on a one-spectrum dump of the
+// 131072-channel workload, with F rounded to fp16 hi + lo alone 4e-6.
+// FIR outputs stay below 2^9 in magnitude and the DFT coefficients below 1,
+// well inside fp16's range. One thread issues the MMAs; tcgen05.commit
+// signals an mbarrier that the CTA waits on with a bounded spin (status word
+// and a clean exit if it gives up). Each thread then reads one row of D with
+// tcgen05.ld (its 16 outputs of one polarisation), multiplies by W_N^(n1 k2)
+// and writes its polarisation's half of each scratch element: this kernel's
+// scratch elements hold (X.re, X.im, Y.re, Y.im), and the 2048-point row
+// kernel reads them in that order (its ZSPLIT form).
+//
+// Shared-memory operands (K-major, no swizzle): 8-row x 16-byte core
+// matrices, element (row r, k) at byte
+//   (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,  SBO = 2 N2 * 16,
+// so the K step between core matrices is 128 bytes and one K = 16 slice of
+// an MMA is 256 bytes further on. The row order above, with the thread order
+// of ColTc::pt_*, puts the eight columns a warp's threads stage for one
+// spectrum and polarisation in eight different rows of one core matrix: the
+// stores are free of bank conflicts.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "vspec_kernels.cuh"
+#include "vspec_tc.cuh"
+
+namespace vspec {
+
+// Power-of-two scaling of the operands, exact in both directions: the FIR
+// coefficients are scaled by 2^4 and F by 2^8, so that the low fp16 parts of
+// small values stay normal numbers (above 2^-14), and the four-step twiddles
+// by 2^-12 to undo both.
+constexpr float kColTcYScale = 16.0f;
+constexpr double kColTcFScale = 256.0;
+constexpr float kColTcUnscale = 1.0f / 4096.0f;
+
+template <int N2>
+struct ColTc {
+    static constexpr int PT = 8, PTS = 512, C = PTS / N2, SPB = 8;
+    static constexpr int K = 2 * N2, NN = 2 * N2;  // MMA K and N
+    static constexpr int ROWS = SPB * 2 * C;       // rows of Y: (spectrum, polarisation, column)
+    static constexpr int MB = ROWS / 128;          // M = 128 blocks
+    static constexpr int SBO = K * 16;             // bytes between 8-row groups
+    static constexpr int APART = ROWS * K * 2;     // bytes of one fp16 part of Y
+    static constexpr int BPART = NN * K * 2;       // bytes of one fp16 part of F
+    static constexpr int KSTEPS = K / 16;
+    static constexpr int TMEM_COLS = MB * NN;      // fp32 columns of one D buffer (two are allocated)
+    // Y hi, Y lo, F hi, F lo, raw frames [2][SPB][PTS] u32, coefficients
+    // [PT][PTS] float, twiddle tile [N2][C] float2
+    static constexpr size_t smem = 2 * (size_t)APART + 2 * (size_t)BPART + 2 * (size_t)SPB * PTS * 4 +
+                                   (size_t)PT * PTS * 4 + (size_t)PTS * 8;
+    static_assert(N2 == 16 || N2 == 32 || N2 == 64, "column lengths of this kernel");
+    static_assert(MB * 128 == ROWS && TMEM_COLS == 128, "2 x 2 accumulators of 128 TMEM columns, whole M blocks");
+    static_assert(KSTEPS % 2 == 0, "two halves of the K slices");
+    // Thread t pre-filters point (n2, c) of the tile, laid out so that every
+    // warp holds 8 consecutive columns x 4 consecutive n2: its stores of Y
+    // then fill 8 rows x 4 words of one core matrix, free of bank conflicts.
+    // The staged frames use the same order (4 consecutive columns stay
+    // adjacent, one 16-byte copy).
+    static constexpr int CB = C / 8;
+    __host__ __device__ static constexpr int pt_n2(int t) { return ((t >> 5) / CB) * 4 + ((t >> 3) & 3); }
+    __host__ __device__ static constexpr int pt_c(int t) { return ((t >> 5) % CB) * 8 + (t & 7); }
+    __host__ __device__ static constexpr int pt_index(int n2, int c) {
+        return ((n2 >> 2) * CB + (c >> 3)) * 32 + (n2 & 3) * 8 + (c & 7);
+    }
+    static_assert(smem <= 232448 - 1024, "shared memory of one CTA");
+    __host__ __device__ static constexpr int off(int r, int k) {
+        return (r >> 3) * SBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+    }
+};
+
+// The column DFT operand F of ColTc<N2> as its shared-memory image, hi part
+// then lo part (from FP64 cosines and sines, rounded once to fp16 each).
+__global__ void gen_coltc_operand_kernel(unsigned char *op, int N2) {
+    const int NN = 2 * N2, K = 2 * N2;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN * K) return;
+    const int n = e / K, k = e % K;            // D column (output), K index (input)
+    const int k2 = n >> 1, n2 = k >> 1;
+    double sn, cs;
+    sincospi(2.0 * (double)((n2 * k2) % N2) / (double)N2, &sn, &cs);
+    // (xr + i xi)(cos - i sin): re gets xr cos + xi sin, im gets -xr sin + xi cos
+    double v;
+    if ((n & 1) == 0) v = (k & 1) ? sn : cs;
+    else v = (k & 1) ? cs : -sn;
+    v *= kColTcFScale;
+    const __half hi = __double2half(v);
+    const __half lo = __double2half(v - (double)__half2float(hi));
+    const int SBO = K * 16;
+    const int o = (n >> 3) * SBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__half *>(op + o) = hi;
+    *reinterpret_cast<__half *>(op + NN * K * 2 + o) = lo;
+}
+
+// hi/lo fp16 split of a complex value as two packed half2 words (re, im)
+__device__ __forceinline__ void split_half2(float re, float im, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(re, im);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// fp16 instruction descriptor of kind::f16: fp32 D (bits 4-5 = 1), fp16 A and
+// B (type 0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t instr_desc_f16(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+template <int N2>
+__global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant__ ColParams p) {
+    using G = ColTc<N2>;
+    using namespace tc;
+    constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
+    extern __shared__ __align__(128) unsigned char smem_ct[];
+    unsigned char *ahi = smem_ct, *alo = ahi + G::APART;
+    unsigned char *fhi = alo + G::APART, *flo = fhi + G::BPART;
+    uint32_t *raw = reinterpret_cast<uint32_t *>(flo + G::BPART);  // [2][SPB][PTS]
+    float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);     // [PT][PTS]
+    float2 *tws = reinterpret_cast<float2 *>(cfs + PT * PTS);        // [N2][C]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int D = PT - p.P;  // leading zero taps
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_slot)), "r"(4u * G::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // F (hi and lo) into shared memory, 16 bytes at a time
+    for (int e = t; e < 2 * G::BPART / 16; e += blockDim.x)
+        reinterpret_cast<uint4 *>(fhi)[e] = __ldg(reinterpret_cast<const uint4 *>(p.dftop) + e);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // the epilogue's share of D: lane quarter q of TMEM, 32 columns from 32 g
+    const int q = warp & 3, g = warp >> 2;
+    const int mb = (32 * g) / G::NN, k0 = ((32 * g) % G::NN) / 2;
+    const int R = mb * 128 + 32 * q + lane;  // row of Y this thread reads back
+    const int ec = R % C, ep = (R / C) & 1, eu = R / (2 * C);
+    const int n2 = G::pt_n2(t), c = G::pt_c(t);  // the point this thread pre-filters
+
+    bool ok = true;
+    uint32_t batches = 0;  // MMA batches committed (mbarrier phase, TMEM buffer)
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
+    for (long long f = sp.lo; f < sp.hi && ok;) {
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        const int n1_0 = x * C;
+        // W_N^(n1 k2) in natural k2 order, times 2^-kScale (undoes the
+        // operands' power-of-two scaling exactly)
+        for (int e = t; e < PTS; e += blockDim.x) {  // tws[k2 C + c]
+            const float2 w = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
+            tws[e] = make_float2(w.x * kColTcUnscale, w.y * kColTcUnscale);
+        }
+        const long long n_pt = n1_0 + c + (long long)p.N1 * n2;
+#pragma unroll
+        for (int k = 0; k < PT; k++)
+            cfs[k * PTS + t] = k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) * kColTcYScale : 0.f;
+        P2 win[PT];
+        const long long sabs = p.s0 + s_beg;
+#pragma unroll
+        for (int k = 0; k < PT - 1; k++) {
+            long long fr = sabs - D + k;
+            if (fr < 0) fr = 0;
+            win[k] = unpack_p2(load_raw<2>(p.in, fr * p.N + n_pt) ^ 0x80808080u);
+        }
+        auto stage = [&](int sb, int buf) {
+            const int nbb = min(SPB, s_end - sb);
+            constexpr int per_row = C / 4, per_frame = PTS / 4;
+            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
+                const int u = e / per_frame, r = e % per_frame;
+                const int rn2 = r / per_row, ch = r % per_row;
+                const long long fr = p.s0 + sb + u + p.P - 1;
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
+                                      (long long)p.N1 * rn2 + ch * 4;
+                uint32_t *dst = raw + (buf * SPB + u) * PTS + G::pt_index(rn2, ch * 4);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // epilogue of a finished batch: this thread's row of D (TMEM buffer
+        // dbuf, the sum of its two K halves), 16 outputs k2 = k0 .. k0 + 15 of
+        // polarisation ep, column ec, spectrum eu of the batch, times
+        // W_N^(n1 k2), into the scratch
+        auto epilogue = [&](int sbase, int nbb, uint32_t dbuf) {
+            float d[32], d1[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + 2u * dbuf * G::TMEM_COLS + (uint32_t)(32 * g);
+            tmem_ld32(ta, d);
+            tmem_ld32(ta + G::TMEM_COLS, d1);
+#pragma unroll
+            for (int i = 0; i < 32; i++) d[i] += d1[i];
+            if (eu < nbb) {
+                float2 *z = reinterpret_cast<float2 *>(reinterpret_cast<P2 *>(p.Z) + (size_t)(sbase + eu) * p.N +
+                                                       n1_0 + ec) + ep;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int k2 = k0 + j;
+                    z[(size_t)k2 * p.N1 * 2] = cmul(make_float2(d[2 * j], d[2 * j + 1]), tws[k2 * C + ec]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        };
+        int pend_base = 0, pend_nb = 0;  // the batch whose MMAs are done and epilogue pending
+        stage(s_beg, 0);
+        for (int s_base = s_beg, buf = 0; s_base < s_end; s_base += SPB, buf ^= 1) {
+            const int nb = min(SPB, s_end - s_base);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // frames visible; the other buffer is free
+            if (s_base + SPB < s_end) stage(s_base + SPB, buf ^ 1);
+            float2 cf2[PT];
+#pragma unroll
+            for (int k = 0; k < PT; k++) cf2[k] = dup2(cfs[k * PTS + t]);
+            // FIR of spectrum u of the batch into rows (2u + p) C + c of Y, K = 2 n2
+            // (the previous batch's MMAs are done with Y: their wait ended the
+            // previous iteration)
+            auto fir_one = [&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                constexpr int snew = (u + PT - 1) % PT;
+                win[snew] = unpack_p2(raw[(buf * SPB + u) * PTS + t] ^ 0x80808080u);
+                const P2 &w0 = win[u % PT];
+                P2 y{__fmul2_rn(cf2[0], w0.re), __fmul2_rn(cf2[0], w0.im)};
+#pragma unroll
+                for (int k = 1; k < PT; k++) {
+                    const P2 &wk = win[(u + k) % PT];
+                    y.re = __ffma2_rn(cf2[k], wk.re, y.re);
+                    y.im = __ffma2_rn(cf2[k], wk.im, y.im);
+                }
+                uint32_t hx, lx, hy, ly;
+                split_half2(y.re.x, y.im.x, hx, lx);
+                split_half2(y.re.y, y.im.y, hy, ly);
+                const int ox = G::off((2 * u) * C + c, 2 * n2), oy = G::off((2 * u + 1) * C + c, 2 * n2);
+                *reinterpret_cast<uint32_t *>(ahi + ox) = hx;
+                *reinterpret_cast<uint32_t *>(alo + ox) = lx;
+                *reinterpret_cast<uint32_t *>(ahi + oy) = hy;
+                *reinterpret_cast<uint32_t *>(alo + oy) = ly;
+            };
+            if (nb == SPB) for_slots(fir_one, std::make_integer_sequence<int, SPB>{});
+            else for_slots_below(fir_one, nb, std::make_integer_sequence<int, SPB>{});
+            // Y is complete: make it visible to the tensor cores, then issue
+            // into TMEM buffer batches & 1 (the other buffer holds the pending batch)
+            fence_proxy_async();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dbuf = batches & 1u;
+            if (t == 0) {
+                constexpr uint32_t idesc = instr_desc_f16(128, G::NN);
+                const unsigned char *as[3] = {ahi, alo, ahi};
+                const unsigned char *bs[3] = {fhi, fhi, flo};
+                // each half of the K slices accumulates in its own TMEM
+                // columns (shorter accumulation chains in the tensor cores);
+                // the epilogue adds the halves in FP32
+#pragma unroll
+                for (int m = 0; m < G::MB; m++) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; hh++) {
+                        uint32_t acc = 0;
+                        const uint32_t dcol = tmem + (2u * dbuf + hh) * G::TMEM_COLS + (uint32_t)(m * G::NN);
+#pragma unroll
+                        for (int term = 0; term < 3; term++) {
+#pragma unroll
+                            for (int ks = hh * G::KSTEPS / 2; ks < (hh + 1) * G::KSTEPS / 2; ks++) {
+                                const uint64_t ad = smem_desc(smem_addr(as[term]) + m * 16 * G::SBO + 256u * ks, 128u, G::SBO);
+                                const uint64_t bd = smem_desc(smem_addr(bs[term]) + 256u * ks, 128u, G::SBO);
+                                mma_bf16(dcol, ad, bd, idesc, acc);
+                                acc = 1;
+                            }
+                        }
+                    }
+                }
+                mma_commit(&mbar);
+            }
+            // the previous batch's epilogue runs while the tensor cores work
+            if (pend_nb > 0) epilogue(pend_base, pend_nb, dbuf ^ 1u);
+            const bool done = mbar_wait(&mbar, dbuf, p.wait_limit);
+            batches++;
+            ok = __syncthreads_and(done);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) break;
+            pend_base = s_base;
+            pend_nb = nb;
+        }
+        if (ok && pend_nb > 0) epilogue(pend_base, pend_nb, (batches - 1) & 1u);
+        __syncthreads();  // the batches are done with the twiddle tile and D
+    }
+    if (!ok && t == 0) atomicExch(p.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        // a batch whose wait gave up has MMAs outstanding: wait for its commit
+        // with the full bound before freeing their tensor memory
+        if (!ok) mbar_wait(&mbar, (batches - 1) & 1u);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(4u * G::TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace vspec

@@ -29,6 +29,7 @@ ERR_DEVICE_TIMEOUT = -6
 PLAN_TWO_KERNEL = 1  # force the general two-kernel path
 PLAN_TENSOR = 2      # first 2048-point row pass on the tensor cores
 PLAN_KAHAN = 4       # compensated accumulation
+PLAN_TENSOR_INT8 = 8  # pre-filter + column DFT as one tensor-core product on the int8 input
 
 _lib = None
 

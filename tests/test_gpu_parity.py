@@ -329,7 +329,12 @@ def test_subband_mode_matches_oracle(oracle_mod, cfg):
 
 @pytest.mark.parametrize("cfg", [(4096, 8, 2, PFB, WIN_HANN, 11), (32768, 8, 2, PFB, WIN_HANN, 30),
                                  (131072, 8, 2, PFB, WIN_HANN, 3), (524288, 1, 2, DIRECT, WIN_RECT, 2),
-                                 (65536, 1, 2, DIRECT, WIN_RECT, 5)])
+                                 (65536, 1, 2, DIRECT, WIN_RECT, 5),
+                                 # tensor-core column DFTs: 16-, 32- and 64-point columns, ragged
+                                 # batches, leading zero taps, windows
+                                 (32768, 5, 2, PFB, WIN_RECT, 13), (65536, 8, 2, PFB, WIN_HANN, 21),
+                                 (65536, 7, 2, PFB, WIN_HAMMING, 4), (131072, 8, 2, PFB, WIN_HANN, 37),
+                                 (131072, 6, 2, PFB, WIN_HANN, 1)])
 def test_tensor_core_plan_matches_oracle(oracle_mod, cfg):
     """First row pass on the tensor cores (bf16 hi/lo): within the tensor-core
     tolerance of the oracle."""
@@ -345,6 +350,41 @@ def test_tensor_core_plan_matches_oracle(oracle_mod, cfg):
           f"{metrics(run_gpu(bank, x), o)['pure']:.3e})")
     with Plan(n, p, npol, mode, win, PLAN_TENSOR) as plan:
         plan.check()
+
+
+@pytest.mark.parametrize("cfg", [(32768, 8, 2, PFB, WIN_HANN, 30), (32768, 5, 2, PFB, WIN_RECT, 13),
+                                 (65536, 8, 2, PFB, WIN_HANN, 21), (65536, 3, 2, PFB, WIN_HANN, 130),
+                                 (131072, 8, 2, PFB, WIN_HANN, 37), (131072, 6, 2, PFB, WIN_HAMMING, 1),
+                                 (32768, 1, 2, DIRECT, WIN_RECT, 300), (65536, 1, 2, DIRECT, WIN_RECT, 5),
+                                 (131072, 1, 2, DIRECT, WIN_HANN, 7)],
+                         ids=lambda c: f"N{c[0]}_P{c[1]}_m{c[3]}_w{c[4]}_S{c[5]}")
+def test_int8_tensor_plan_matches_oracle(oracle_mod, cfg):
+    """Pre-filter and column DFT as one tensor-core product on the int8
+    input (128-spectrum blocks with ragged ends, fewer taps than the frame
+    operand holds, windows, direct mode): within the tensor-core tolerance;
+    the compensated form too."""
+    from parity_util import ATOL_TC, metrics
+    from paper_1411_0436_gb300.vspec import PLAN_KAHAN, PLAN_TENSOR_INT8, Plan
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3, tones=(Tone(40.0, n * 0.2 + 0.37, (0, 1)),))
+    x = workloads.generate(bank, 321 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    m = assert_close(run_gpu(bank, x, flags=PLAN_TENSOR_INT8), o, atol=ATOL_TC, what=f"{cfg} int8 tensor")
+    assert_close(run_gpu(bank, x, flags=PLAN_TENSOR_INT8 | PLAN_KAHAN), o, atol=ATOL_TC, what=f"{cfg} int8+kahan")
+    print(f"\n{cfg}: normalised max error {m['pure']:.3e} (fp32 path: "
+          f"{metrics(run_gpu(bank, x), o)['pure']:.3e})")
+    with Plan(n, p, npol, mode, win, PLAN_TENSOR_INT8) as plan:
+        assert "A=tensor-int8" in plan.describe()
+        plan.check()
+
+
+def test_int8_tensor_plan_rejects_other_sizes():
+    from paper_1411_0436_gb300 import vspec
+    for args in [(16384, 8, 2, PFB, WIN_HANN), (262144, 8, 2, PFB, WIN_HANN), (32768, 8, 1, PFB, WIN_HANN),
+                 (32768, 12, 2, PFB, WIN_HANN)]:
+        with pytest.raises(vspec.VspecError) as e:
+            vspec.Plan(*args, flags=vspec.PLAN_TENSOR_INT8)
+        assert e.value.status == vspec.ERR_UNSUPPORTED
 
 
 def test_tensor_core_plan_rejects_other_sizes():
