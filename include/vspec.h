@@ -160,6 +160,19 @@ VSPEC_API vspec_status vspec_plan_check(vspec_plan *plan);
  * bounded device-side waits), VSPEC_ERR_CUDA.
  */
 VSPEC_API vspec_status vspec_set_wait_limit(long long polls);
+
+/*
+ * Bounds checks of the debug build. The library built with -DVSPEC_DEBUG
+ * (libvspec_debug.so) checks, before every access of the chunk scratch, the
+ * partial-sum slots and the input frames, that the index lies inside the
+ * buffer the plan or the call owns; a failed check sets a bit of a device
+ * status word and the access is skipped (no trap). Bits: 1 chunk-scratch
+ * index, 2 input frame, 4 partial-sum slot, 8 tile index.
+ * vspec_debug_flags synchronises the device, writes that word to *flags and,
+ * if clear != 0, resets it. The release build returns VSPEC_ERR_UNSUPPORTED.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_CUDA, VSPEC_ERR_UNSUPPORTED.
+ */
+VSPEC_API vspec_status vspec_debug_flags(unsigned *flags, int clear);
 VSPEC_API vspec_status vspec_plan_inject_timeout(vspec_plan *plan);
 
 /* Release a plan and all device memory it owns. NULL is accepted. The caller

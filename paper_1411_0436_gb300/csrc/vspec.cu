@@ -1236,6 +1236,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     ca.tiles = p->N1 / p->C;
     ca.G = p->tileG;
     ca.win = p->mode == VSPEC_DIRECT && p->window != VSPEC_WIN_RECT;
+    ca.nframes = (long long)nspectra + (p->mode == VSPEC_PFB ? p->P : 1) - 1;
     ca.dftop = p->dftop;
     ca.status = p->tc_status;
     ca.wait_limit = g_wait_limit.load();
@@ -1260,6 +1261,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     cb.coef = p->coef;
     cb.P = p->P;
     cb.store = store;
+    cb.nframes = ca.nframes;
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);
@@ -1451,6 +1453,24 @@ vspec_status vspec_plan_check(vspec_plan *plan) {
     VSPEC_CUDA(cudaMemset(plan->tc_status, 0, sizeof(int)));
     g_last_error = "a bounded wait for the tensor cores expired";
     return VSPEC_ERR_DEVICE_TIMEOUT;
+}
+
+vspec_status vspec_debug_flags(unsigned *flags, int clear) {
+#ifdef VSPEC_DEBUG
+    if (!flags) return VSPEC_ERR_INVALID_ARG;
+    VSPEC_CUDA(cudaDeviceSynchronize());
+    VSPEC_CUDA(cudaMemcpyFromSymbol(flags, vspec::g_debug_flags, sizeof(unsigned)));
+    if (clear) {
+        const unsigned zero = 0;
+        VSPEC_CUDA(cudaMemcpyToSymbol(vspec::g_debug_flags, &zero, sizeof(unsigned)));
+    }
+    return VSPEC_OK;
+#else
+    (void)flags;
+    (void)clear;
+    g_last_error = "bounds checks are compiled only into the debug build (VSPEC_DEBUG)";
+    return VSPEC_ERR_UNSUPPORTED;
+#endif
 }
 
 vspec_status vspec_set_wait_limit(long long polls) {
@@ -1781,6 +1801,7 @@ extern "C" vspec_status vspec_execute_noalloc(const int8_t *d_in, int nchan, int
     cb.tiles = c.N2 / c.RB;
     cb.slots = c.slots;
     ca.tiles = c.N1 / c.C;
+    ca.nframes = cb.nframes = (long long)nspectra + c.P - 1;
 
     const int sc_full = std::min(nspectra, c.sc_max);
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {

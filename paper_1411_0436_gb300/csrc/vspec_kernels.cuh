@@ -32,6 +32,24 @@ namespace vspec {
 
 constexpr int kMaxPasses = 6;
 
+// Bounds checks of the debug build (compiled with -DVSPEC_DEBUG): a failed
+// check sets its bit in g_debug_flags and the guarded access is skipped;
+// nothing traps. In the release build dbg_ok is `true` and costs nothing.
+//   bit 0: chunk-scratch index (spectrum, row position, column) out of range
+//   bit 1: input frame past the call's input
+//   bit 2: partial-sum slot or position out of range
+//   bit 3: tile index out of range
+enum : unsigned { kDbgScratch = 1u, kDbgInput = 2u, kDbgSlot = 4u, kDbgTile = 8u };
+#ifdef VSPEC_DEBUG
+__device__ unsigned int g_debug_flags;
+__device__ __forceinline__ bool dbg_ok(bool cond, unsigned bit) {
+    if (!cond) atomicOr(&g_debug_flags, bit);
+    return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_ok(bool, unsigned) { return true; }
+#endif
+
 template <int NPOL> struct Elem;
 template <> struct Elem<1> {
     using T = float2;     // one complex sample
@@ -61,6 +79,7 @@ struct ColParams {
     int *status;                 // set to 1 if a bounded wait for the tensor cores gave up
     unsigned wait_limit;         // polls of that wait
     int bterms;                  // fp16 parts of the fused tensor-core operand: 1 (hi) or 2 (hi, lo)
+    long long nframes;           // frames the call's input holds (bounds checks of debug builds)
 };
 
 struct RowParams {
@@ -81,6 +100,7 @@ struct RowParams {
     int P;
     long long s0;        // absolute index of the chunk's first spectrum
     int store;           // 1: every slot has exactly one writer this call, which stores (no zeroing)
+    long long nframes;   // frames the call's input holds (bounds checks of debug builds)
 };
 
 // ------------------------------------------------------------ work split --
@@ -176,7 +196,7 @@ __device__ __forceinline__ void col_butterfly(const ColParams &p, typename Elem<
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const size_t zi = (size_t)(base + q) * p.N1 + n1;
-            Zs[zi] = cmul(v[q], tws[(base + q) * C + c]);
+            if (dbg_ok(base + q < p.N2 && n1 < p.N1, kDbgScratch)) Zs[zi] = cmul(v[q], tws[(base + q) * C + c]);
         }
     }
 }
@@ -297,7 +317,8 @@ __device__ __forceinline__ void fir_colfft_segment(const ColParams &p, typename 
         if (f < 0) f = 0;
 #pragma unroll
         for (int i = 0; i < PPT; i++) {
-            const uint32_t wx = load_raw<NPOL>(p.in, f * p.N + n_pt[i]) ^ 0x80808080u;
+            const uint32_t wx = dbg_ok(f < p.nframes, kDbgInput) ? load_raw<NPOL>(p.in, f * p.N + n_pt[i]) ^ 0x80808080u
+                                                               : 0x80808080u;
             if constexpr (kPacked) {
                 win2[i][t] = unpack_p2(wx);
             } else {
@@ -495,7 +516,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
         for (int k = 0; k < PT - 1; k++) {
             long long fr = sabs - D + k;
             if (fr < 0) fr = 0;
-            win[k] = unpack_p2(load_raw<2>(p.in, fr * p.N + n_pt) ^ 0x80808080u);
+            win[k] = unpack_p2((dbg_ok(fr < p.nframes, kDbgInput) ? load_raw<2>(p.in, fr * p.N + n_pt) : 0u) ^ 0x80808080u);
         }
         // the newest frames of SPB spectra, one batch ahead, 16-byte copies
         auto stage = [&](int sb, int buf) {
@@ -508,8 +529,9 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
                                       (long long)p.N1 * n2 + ch * 4;
                 uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+                if (dbg_ok(fr < p.nframes, kDbgInput))
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
@@ -550,6 +572,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                         for (int q = 0; q < N2; q++) v[q] = data[sb * SS + q * C + c];
                         Dft<N2>::run(v);
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
                         for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(q, c)]);
@@ -588,6 +611,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
                         Dft<R2>::run(v);
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
                         for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(b * R2 + q, c)]);
                     }
@@ -667,8 +691,9 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
                                       (long long)p.N1 * n2 + ch * 4;
                 uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+                if (dbg_ok(fr < p.nframes, kDbgInput))
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
@@ -690,6 +715,7 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
                         for (int q = 0; q < N2; q++) v[q] = sample(rb + sb * PTS, q * C + c);
                         Dft<N2>::run(v);
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
                         for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
@@ -727,6 +753,7 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
                         Dft<R2>::run(v);
                         P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
                         for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[(b * R2 + q) * C + c]);
                     }
@@ -1014,7 +1041,8 @@ __global__ void __launch_bounds__(256, 2) rowfft_detect_kernel(const __grid_cons
         auto flush = [&](bool store) {
             const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N;
             A *part = reinterpret_cast<A *>(p.partial) + so;
-            for (int e = threadIdx.x; e < nacc; e += blockDim.x) {
+            const bool slot_ok = dbg_ok(span_slot(p.tiles, p.sc, x) < p.slots && x < p.tiles, kDbgSlot);
+            for (int e = threadIdx.x; e < nacc && slot_ok; e += blockDim.x) {
                 const int q = e >> lU, w = e & ((1 << lU) - 1);
                 const int r = w >> lq, b = w & ((1 << lq) - 1);
                 const size_t o = (size_t)(x * p.RB + r) * p.N1 + b * RL + q;
@@ -1136,10 +1164,13 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<
                 const float4 e = zr[ht + 128 * q];
                 v[q] = make_p2(e.x, e.y, e.z, e.w);
             }
-        } else {
+        } else if (dbg_ok(s < p.sc && (x + 1) * 2048 <= p.N, kDbgScratch | kDbgTile)) {
             const T *zr = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] = zr[ht + 128 * q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] = T{};
         }
         Dft<16>::run(v);
         const float2 *tw = p.twB + ps.off + ht * 15;
@@ -1215,6 +1246,7 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
         // add the registers into this block's slot (thread t holds positions
         // 8t .. 8t+7 of row tile x); `store`: the slot's first write this call
         auto flush = [&](bool store) {
+            if (!dbg_ok(span_slot(p.tiles, p.sc, x) < p.slots && (x + 1) * 2048 <= p.N, kDbgSlot)) return;
             const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
             A *part = reinterpret_cast<A *>(p.partial) + so;
 #pragma unroll

@@ -64,12 +64,17 @@ NEVER = 2 ** 31 - 1  # two_kernel_from value: never switch to the two-kernel pat
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libvspec.so (building it with nvcc first if it is missing)."""
+    """Load libvspec.so (building it with nvcc first if it is missing).
+
+    VSPEC_LIBRARY=debug in the environment loads libvspec_debug.so instead:
+    the same library with bounds checks into a device status word
+    (vspec_debug_flags)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        debug = os.environ.get("VSPEC_LIBRARY", "") == "debug"
+        path = _build.LIB_DEBUG if debug else _build.LIB
         if build_if_missing:
-            path = _build.build()
+            _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing; run paper_1411_0436_gb300.build.build()")
         lib = ctypes.CDLL(path)
@@ -109,6 +114,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_bank_tuning.restype = i
         lib.vspec_plan_check.argtypes = [vp]
         lib.vspec_plan_check.restype = i
+        lib.vspec_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint), i]
+        lib.vspec_debug_flags.restype = i
         lib.vspec_set_wait_limit.argtypes = [ctypes.c_longlong]
         lib.vspec_set_wait_limit.restype = i
         lib.vspec_plan_inject_timeout.argtypes = [vp]
@@ -287,6 +294,15 @@ def vspec_execute_noalloc(d_in, nchan: int, ntaps: int, npol: int, mode: int, wi
                                       _addr(d_accum), _stream(stream))
     if st != OK:
         raise VspecError(st, "vspec_execute_noalloc")
+
+
+def vspec_debug_flags(clear: bool = True) -> int:
+    """The debug build's bounds-check status word (raises on the release build)."""
+    w = ctypes.c_uint(0)
+    st = load().vspec_debug_flags(ctypes.byref(w), int(clear))
+    if st != OK:
+        raise VspecError(st, "vspec_debug_flags")
+    return int(w.value)
 
 
 def vspec_set_wait_limit(polls: int) -> None:
