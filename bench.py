@@ -523,6 +523,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                                  variants["fp32_default"]["value"])
 
     plan.close()
+    # the batched multi-beam workload (rank 0 at N=1), as an extra key
+    batched = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        batched = measure_batch(max(3, min(args.steps, 50)), 3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GHz", "n_gpus": world,
@@ -559,6 +563,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "cpu_baseline": cpu,
             "tc_vs_fp32": variants,
             "cufft_comparison": cufft,
+            "batched_c5": batched,
             "parity": parity,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} | {"samples": clk["samples"]},
             "complex_gsps": 2 * value,
@@ -566,10 +571,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def measure_batch(steps: int, warmup: int) -> dict:
     """The batched multi-beam workload (eight banks, 1024..524288 channels,
     PFB and direct alternating, uneven integrations) as one CUDA-graph launch
-    per step after the autotuner has picked each bank's kernel path."""
+    per step after the autotuner has picked each bank's plan form, four-step
+    split and launch shape."""
     import torch
     from paper_1411_0436_gb300.vspec import Batch
     dev = torch.device("cuda", 0)
@@ -581,15 +587,16 @@ def run_batch(args):
     ns = [b.nspectra for b in banks]
     stream = torch.cuda.current_stream(dev)
     flags = batch.autotune(d_in, ns, accs, stream, reps=3)
-    batch_shapes = [batch.bank_tuning(i)[1] for i in range(len(flags))]
+    batch_shapes = [dict(batch.bank_tuning(i)[1], col_len=batch.bank_shape(i)[0], tile_cols=batch.bank_shape(i)[1])
+                    for i in range(len(flags))]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.fill_(1)
         batch.execute(d_in, ns, accs, stream)
     torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
         flush.fill_(i & 0xFF)
         starts[i].record(stream)
         batch.execute(d_in, ns, accs, stream)
@@ -597,23 +604,31 @@ def run_batch(args):
     torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     samples = sum(b.nspectra * b.nchan for b in banks)
-    value = args.steps * samples / (total_ms * 1e-3) / 1e9
+    value = steps * samples / (total_ms * 1e-3) / 1e9
     in_bytes = sum(x.nbytes for x in xs)
     peak, peak_kind = _peaks()
-    achieved = args.steps * sum(b.nbytes + 2 * b.nchan * 16 for b in banks) / (total_ms * 1e-3) / 1e9
+    achieved = steps * sum(b.nbytes + 2 * b.nchan * 16 for b in banks) / (total_ms * 1e-3) / 1e9
     batch.close()
+    return {"value": value, "unit": "GHz", "steps": steps, "ms_per_step": total_ms / steps,
+            "workload": "8 dual-pol banks 1024..524288 channels, PFB-8/direct alternating, "
+                        "2048..64 spectra, one CUDA-graph launch per step",
+            "input_bytes": int(in_bytes), "bank_flags": flags, "bank_shapes": batch_shapes,
+            "path_roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                              "peak_source": peak_kind}}
+
+
+def run_batch(args):
+    """--config c5: the batched workload as the bench line."""
+    r = measure_batch(args.steps, args.warmup)
     print(json.dumps({
-        "metric": METRIC + " (batched multi-beam workload)", "value": value, "unit": "GHz",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": METRIC + " (batched multi-beam workload)", "value": r["value"], "unit": "GHz",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "8 dual-pol banks 1024..524288 channels, PFB-8/direct alternating, "
-                               "2048..64 spectra, one CUDA-graph launch per step",
-                   "input_bytes": int(in_bytes), "bank_flags": flags,
-                   "bank_shapes": [batch_shapes[i] for i in range(len(flags))],
+        "config": {"workload": r["workload"], "input_bytes": r["input_bytes"], "bank_flags": r["bank_flags"],
+                   "bank_shapes": r["bank_shapes"],
                    "l2": "flushed between steps (256 MiB write outside the timed interval)"},
-        "path_roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                          "peak_source": peak_kind},
+        "path_roofline": r["path_roofline"],
     }), flush=True)
 
 

@@ -117,6 +117,23 @@ VSPEC_API vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int nta
                                             vspec_mode mode, vspec_window window, unsigned flags);
 
 /*
+ * vspec_plan_create_ex with an explicit shape of the two-kernel path (for the
+ * batch autotuner and experiments): col_len is the column length N2 of the
+ * four-step split (rows of nchan / col_len points, at most 4096), tile_cols
+ * the width in columns of kernel A's tiles (which selects the general kernel
+ * A); 0 keeps the plan's own choice of each. A non-zero shape implies
+ * VSPEC_PLAN_TWO_KERNEL. Results agree with the default plan's within the
+ * FP32 tolerance. Errors: as vspec_plan_create_ex, and VSPEC_ERR_UNSUPPORTED
+ * for a shape the kernels cannot hold (the reason in vspec_last_error).
+ * vspec_plan_get_shape reports a plan's col_len and tile_cols (0 for a
+ * one-pass fused plan without a two-kernel plan).
+ */
+VSPEC_API vspec_status vspec_plan_create_shaped(vspec_plan **out, int nchan, int ntaps, int npol,
+                                                vspec_mode mode, vspec_window window, unsigned flags,
+                                                int col_len, int tile_cols);
+VSPEC_API vspec_status vspec_plan_get_shape(const vspec_plan *plan, int *col_len, int *tile_cols);
+
+/*
  * Plan for a sub-band mode: nsub sub-bands (1..16) of nchan channels each,
  * every one channelized like a plan of vspec_plan_create_ex. VEGAS's
  * eight-sub-band modes (§3, Table 1) run 16 FFTs in parallel: 8 sub-bands x
@@ -433,14 +450,18 @@ VSPEC_API vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *con
 
 /*
  * Autotuner: for each bank, time `reps` executions (after one warm-up) of
- * every candidate on the given arguments and keep the fastest: the default
- * plan and the two-kernel plan (VSPEC_PLAN_TWO_KERNEL), each in several launch
- * shapes (vspec_plan_set_tuning): its default, a chunk half as long, kernel B
- * over two waves of CTAs, and for a plan that can switch between the fused
- * and the two-kernel path, each path alone. Clears every d_accum[i]
+ * every candidate on the given arguments and keep the fastest. Plan
+ * candidates: the default plan, the two-kernel plan (VSPEC_PLAN_TWO_KERNEL),
+ * and the two-kernel plan with its four-step split moved one factor of two
+ * either way and with the general kernel A at twice or half its tile width
+ * (vspec_plan_create_shaped). Each in several launch shapes
+ * (vspec_plan_set_tuning): its default, chunks a half and a quarter as long,
+ * kernel B over two waves of CTAs, and for a plan that can switch between the
+ * fused and the two-kernel path, each path alone. Clears every d_accum[i]
  * afterwards and synchronises `stream`. vspec_batch_bank_flags reports the
  * VSPEC_PLAN_* flags of the plan chosen for bank `bank`;
- * vspec_batch_bank_tuning also its launch shape (either pointer may be NULL).
+ * vspec_batch_bank_tuning also its launch shape and vspec_batch_bank_shape its
+ * split and tile width (vspec_plan_get_shape); output pointers may be NULL.
  */
 VSPEC_API vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
                                             const int *nspectra, float *const *d_accum,
@@ -448,6 +469,7 @@ VSPEC_API vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *co
 VSPEC_API vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags);
 VSPEC_API vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigned *flags,
                                                vspec_tuning *tuning);
+VSPEC_API vspec_status vspec_batch_bank_shape(const vspec_batch *batch, int bank, int *col_len, int *tile_cols);
 
 /*
  * Batched 16-point DFTs on the tensor cores (tcgen05.mma, bf16 operands,

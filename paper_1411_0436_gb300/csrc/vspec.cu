@@ -123,6 +123,7 @@ struct vspec_plan {
     int N = 0, P = 0, npol = 0, mode = 0, window = 0, device = 0;
     int N1 = 0, N2 = 0, C = 0, PT = 0, PPT = 0, TA = 0, RB = 0, TB = 0;
     int tileG = 1;                   // kernel-A tiles per group (tile_split)
+    int req_n2 = 0, req_cols = 0;    // requested column length / kernel-A tile columns (0: the plan's choice)
     const char *formA = "general";   // kernel A's form (vspec_plan_describe)
     const char *formB = "general";   // kernel B's form
     int num_sms = 0, occA = 1, occB = 1;
@@ -606,6 +607,18 @@ vspec_status build_plan(vspec_plan *p) {
         PT = 1;
         grow();
     }
+    if (p->req_n2) {  // a requested four-step split (vspec_plan_create_shaped)
+        const int n2 = p->req_n2;
+        const bool gather = pfb && N / n2 > 4096;
+        const int cap = gather ? 4096 / cmin : n2max();
+        if (!is_pow2(n2) || n2 > N || n2 > cap || N / n2 > 4096) {
+            g_last_error = "requested column length outside what kernel A holds (N1 = nchan / col_len <= 4096)";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        N2 = n2;
+        p->gather = gather;
+        if (gather) PT = 1;
+    }
     const int N1 = N / N2;
     if (N1 > 4096) {
         g_last_error = "nchan too large for this mode in this build";
@@ -621,15 +634,23 @@ vspec_status build_plan(vspec_plan *p) {
     // in tiles of 2048 points
     size_t smem_coldir = 0;
     std::vector<int> r_coldir;
-    const void *coldir = p->npol == 2 && !pfb && N1 == 2048 && N2 >= 2 && N2 <= 256
+    const void *coldir = p->npol == 2 && !pfb && N1 == 2048 && N2 >= 2 && N2 <= 256 && !p->req_cols
                              ? pick_kernel_coldir(N2, &smem_coldir, &r_coldir) : nullptr;
     if (coldir) C = 2048 / N2;
     // dual-pol PFB (5 .. 8 taps) with 2048-point rows (4096 at 2^19): the
     // register-column kernel A in 512-point tiles (for N2 = 128 rows of 4
     // samples, which the tile groups read a whole line at a time)
     const bool colreg_tiles = p->npol == 2 && pfb && PT == 8 && !p->gather && (N1 == 2048 || N1 == 4096) && N2 >= 2 &&
-                              N2 <= 128;
+                              N2 <= 128 && !p->req_cols;
     if (colreg_tiles) C = 512 / N2;
+    if (p->req_cols) {  // a requested tile width: the general kernel A
+        const int c = p->req_cols;
+        if (!is_pow2(c) || c < cmin || c > N1 || (long long)c * N2 > 4096 || N2 == 1) {
+            g_last_error = "requested tile columns out of range (power of two, 32-byte rows, at most 4096 points)";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        C = c;
+    }
     const int pts = N2 * C;
     const int TA = std::min(512, pts);
     const int PPT = pts / TA;
@@ -671,7 +692,7 @@ vspec_status build_plan(vspec_plan *p) {
     // tiles: the register-column kernel A and its own column pass list
     size_t smem_colreg = 0;
     std::vector<int> r_colreg;
-    const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512
+    const void *colreg = p->npol == 2 && pfb && PT == 8 && PPT == 1 && !p->gather && N2 * C == 512 && !p->req_cols
                              ? pick_kernel_colreg(N2, &smem_colreg, &r_colreg) : nullptr;
     if (colreg) {
         p->kernelA = colreg;
@@ -943,7 +964,24 @@ static vspec_status setup_assist(vspec_plan *p) {
 
 vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
                                   vspec_window window, unsigned flags) {
+    return vspec_plan_create_shaped(out, nchan, ntaps, npol, mode, window, flags, 0, 0);
+}
+
+vspec_status vspec_plan_get_shape(const vspec_plan *plan, int *col_len, int *tile_cols) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    const vspec_plan *t = plan->fused && plan->assist ? plan->assist : plan;
+    if (col_len) *col_len = plan->fused && !plan->assist ? 0 : t->N2;
+    if (tile_cols) *tile_cols = plan->fused && !plan->assist ? 0 : t->C;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_create_shaped(vspec_plan **out, int nchan, int ntaps, int npol, vspec_mode mode,
+                                      vspec_window window, unsigned flags, int col_len, int tile_cols) {
     if (!out) return VSPEC_ERR_INVALID_ARG;
+    if (col_len < 0 || tile_cols < 0) {
+        *out = nullptr;
+        return VSPEC_ERR_INVALID_ARG;
+    }
     *out = nullptr;
     if (!is_pow2(nchan) || nchan < 16 || nchan > (1 << 20)) return VSPEC_ERR_INVALID_ARG;
     if (npol != 1 && npol != 2) return VSPEC_ERR_INVALID_ARG;
@@ -966,6 +1004,9 @@ vspec_status vspec_plan_create_ex(vspec_plan **out, int nchan, int ntaps, int np
         return VSPEC_ERR_INVALID_ARG;
     }
     p->flags = flags;
+    p->req_n2 = col_len;
+    p->req_cols = tile_cols;
+    if (col_len || tile_cols) p->flags |= VSPEC_PLAN_TWO_KERNEL;  // a shape is a two-kernel shape
     vspec_status st = build_plan(p);
     if (st == VSPEC_OK && p->fused) st = setup_assist(p);
     if (st != VSPEC_OK) {

@@ -178,23 +178,52 @@ vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
     };
     for (int i = 0; i < batch->nbanks && result == VSPEC_OK; i++) {
         const vspec_bank &d = batch->desc[i];
-        const unsigned cand[2] = {0u, VSPEC_PLAN_TWO_KERNEL};
+        // plan candidates: the default plan, the two-kernel plan, and the
+        // two-kernel plan with the four-step split moved one factor of two
+        // either way (rows twice or half as long) and with the general
+        // kernel A at twice or half the default tile width
+        struct Cand {
+            unsigned flags;
+            int col_len, tile_cols;
+        };
+        std::vector<Cand> cand{{0u, 0, 0}, {VSPEC_PLAN_TWO_KERNEL, 0, 0}};
+        {
+            vspec_plan *probe = nullptr;
+            int n2 = 0, cols = 0;
+            if (vspec_plan_create_ex(&probe, d.nchan, d.ntaps, d.npol, d.mode, d.window, VSPEC_PLAN_TWO_KERNEL) ==
+                VSPEC_OK) {
+                vspec_plan_get_shape(probe, &n2, &cols);
+                vspec_plan_destroy(probe);
+            }
+            if (n2 > 1) {
+                cand.push_back({VSPEC_PLAN_TWO_KERNEL, n2 * 2, 0});
+                cand.push_back({VSPEC_PLAN_TWO_KERNEL, n2 / 2, 0});
+                cand.push_back({VSPEC_PLAN_TWO_KERNEL, n2, cols * 2});
+                if (cols > 1) cand.push_back({VSPEC_PLAN_TWO_KERNEL, n2, cols / 2});
+            }
+        }
         float best = 1e30f;
         vspec_plan *best_plan = nullptr;
         unsigned best_flags = 0;
         vspec_tuning best_tuning{};
-        for (unsigned f : cand) {
+        for (const Cand &cd : cand) {
+            const unsigned f = cd.flags;
             vspec_plan *p = nullptr;
-            if (vspec_plan_create_ex(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window, f) != VSPEC_OK) continue;
-            // launch shapes: the plan's default, a chunk half as long, kernel B
-            // over two waves of CTAs, and for a fused plan each path alone
+            if (vspec_plan_create_shaped(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window, f, cd.col_len,
+                                         cd.tile_cols) != VSPEC_OK)
+                continue;  // a shape the kernels cannot hold
+            // launch shapes: the plan's default, a chunk a half and a quarter
+            // as long, kernel B over two waves of CTAs, and for a fused plan
+            // each path alone
             vspec_tuning def{}, lim{};
             vspec_plan_get_tuning(p, &def, &lim);
             std::vector<vspec_tuning> shapes{def};
-            if (def.chunk_spectra > 1) {
-                vspec_tuning t = def;
-                t.chunk_spectra = def.chunk_spectra / 2;
-                shapes.push_back(t);
+            for (int div : {2, 4}) {
+                if (def.chunk_spectra >= div) {
+                    vspec_tuning t = def;
+                    t.chunk_spectra = def.chunk_spectra / div;
+                    shapes.push_back(t);
+                }
             }
             if (def.chunk_spectra > 0 && lim.blocks_b >= 2) {
                 vspec_tuning t = def;
@@ -255,6 +284,11 @@ vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigne
     if (flags) *flags = batch->flags[bank];
     if (tuning) return vspec_plan_get_tuning(batch->plans[bank], tuning, nullptr);
     return VSPEC_OK;
+}
+
+vspec_status vspec_batch_bank_shape(const vspec_batch *batch, int bank, int *col_len, int *tile_cols) {
+    if (!batch || bank < 0 || bank >= batch->nbanks) return VSPEC_ERR_INVALID_ARG;
+    return vspec_plan_get_shape(batch->plans[bank], col_len, tile_cols);
 }
 
 vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags) {

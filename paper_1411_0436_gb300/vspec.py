@@ -112,6 +112,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_bank_flags.restype = i
         lib.vspec_batch_bank_tuning.argtypes = [vp, i, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(VspecTuning)]
         lib.vspec_batch_bank_tuning.restype = i
+        lib.vspec_batch_bank_shape.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.vspec_batch_bank_shape.restype = i
+        lib.vspec_plan_create_shaped.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, ctypes.c_uint, i, i]
+        lib.vspec_plan_create_shaped.restype = i
+        lib.vspec_plan_get_shape.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.vspec_plan_get_shape.restype = i
         lib.vspec_plan_check.argtypes = [vp]
         lib.vspec_plan_check.restype = i
         lib.vspec_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint), i]
@@ -334,12 +340,31 @@ class Plan:
     """Owns one vspec plan; checks tensor shapes before calling the library."""
 
     def __init__(self, nchan: int, ntaps: int = 8, npol: int = 2, mode: int = PFB,
-                 window: int = WIN_HANN, flags: int = 0, nsub: int = 1):
+                 window: int = WIN_HANN, flags: int = 0, nsub: int = 1, col_len: int = 0,
+                 tile_cols: int = 0):
         self.nchan, self.ntaps, self.npol, self.mode, self.window = nchan, ntaps, npol, mode, window
         self.nsub = nsub
         self.taps_used = 1 if mode == DIRECT else ntaps
         self.handle = None
-        self.handle = vspec_plan_create_sb(nchan, ntaps, npol, nsub, mode, window, flags)
+        if col_len or tile_cols:  # an explicit two-kernel shape (vspec_plan_create_shaped)
+            if nsub != 1:
+                raise ValueError("shaped plans have one sub-band")
+            h = ctypes.c_void_p()
+            st = load().vspec_plan_create_shaped(ctypes.byref(h), nchan, ntaps, npol, mode, window, flags,
+                                                 col_len, tile_cols)
+            if st != OK:
+                raise VspecError(st, "vspec_plan_create_shaped")
+            self.handle = h.value
+        else:
+            self.handle = vspec_plan_create_sb(nchan, ntaps, npol, nsub, mode, window, flags)
+
+    def shape(self):
+        """(column length N2, kernel-A tile columns) of the two-kernel path."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        st = load().vspec_plan_get_shape(self.handle, ctypes.byref(a), ctypes.byref(b))
+        if st != OK:
+            raise VspecError(st, "vspec_plan_get_shape")
+        return int(a.value), int(b.value)
 
     @property
     def out_floats(self) -> int:
@@ -480,6 +505,14 @@ class Batch:
             load().vspec_batch_bank_flags(self.handle, i, ctypes.byref(f))
             out.append(int(f.value))
         return out
+
+    def bank_shape(self, i: int):
+        """(column length N2, kernel-A tile columns) of the plan bank i runs."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        st = load().vspec_batch_bank_shape(self.handle, i, ctypes.byref(a), ctypes.byref(b))
+        if st != OK:
+            raise VspecError(st, "vspec_batch_bank_shape")
+        return int(a.value), int(b.value)
 
     def bank_tuning(self, i: int):
         """(flags, launch shape as a dict) of the plan bank i runs."""

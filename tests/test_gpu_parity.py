@@ -268,9 +268,11 @@ def test_batch_graph_matches_single_banks(oracle_mod):
         ns = [b.nspectra for b in banks]
         flags = batch.autotune(d_in, ns, accs, reps=2)
         assert len(flags) == len(banks)
-        for i, f in enumerate(flags):  # the chosen plan form and launch shape are reported
+        for i, f in enumerate(flags):  # the chosen plan form, split and launch shape are reported
             f2, shape = batch.bank_tuning(i)
             assert f2 == f and shape["blocks_a"] >= 0 and shape["blocks_b"] >= 0
+            n2, cols = batch.bank_shape(i)
+            print(f"\nbank {banks[i].nchan}: flags {f} col_len {n2} tile_cols {cols} {shape}")
         for rep in range(3):   # capture, replay, replay
             for a in accs:
                 a.zero_()
@@ -283,6 +285,36 @@ def test_batch_graph_matches_single_banks(oracle_mod):
         torch.cuda.synchronize()
         for a, a2 in zip(accs, accs2):
             assert torch.equal(a, a2)
+
+
+@pytest.mark.parametrize("cfg,shapes", [
+    ((32768, 8, 2, PFB, WIN_HANN, 21), [(8, 0), (16, 0), (32, 0), (64, 0), (16, 16), (16, 64)]),
+    ((65536, 1, 2, DIRECT, WIN_RECT, 7), [(16, 0), (64, 0), (128, 0), (32, 64), (32, 128)]),
+    ((8192, 3, 1, PFB, WIN_HAMMING, 9), [(2, 0), (8, 0), (4, 32), (4, 256)]),
+], ids=["pfb32768", "direct65536", "single8192"])
+def test_shaped_plans_match_oracle(oracle_mod, cfg, shapes):
+    """Other four-step splits and kernel-A tile widths (the autotuner's
+    candidates) give the oracle's spectrum; shapes the kernels cannot hold
+    are refused."""
+    from paper_1411_0436_gb300 import vspec
+    n, p, npol, mode, win, s = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0, tones=(Tone(30.0, n * 0.13 + 0.3, (0,)),))
+    x = workloads.generate(bank, 61 + n)
+    o = run_oracle(oracle_mod, bank, x)
+    d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
+    for n2, cols in shapes:
+        with vspec.Plan(n, p, npol, mode, win, col_len=n2, tile_cols=cols) as plan:
+            got_n2, got_cols = plan.shape()
+            assert got_n2 == n2 and (cols == 0 or got_cols == cols), (plan.describe(), n2, cols)
+            acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+            plan.execute(d_in, s, acc)
+            torch.cuda.synchronize()
+            g = acc.cpu().numpy().astype(np.float64)
+        assert_close(g.reshape(n, 4) if npol == 2 else g, o, what=f"{cfg} shape {n2, cols}")
+    for n2, cols in [(n, 0), (3, 0), (0, 3), (16, 1 << 14)]:
+        with pytest.raises(vspec.VspecError) as e:
+            vspec.Plan(n, p, npol, mode, win, col_len=n2, tile_cols=cols)
+        assert e.value.status in (vspec.ERR_UNSUPPORTED, vspec.ERR_INVALID_ARG)
 
 
 def test_plans_of_different_sizes_coexist():
