@@ -380,6 +380,18 @@ VSPEC_API vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tunin
 VSPEC_API vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *tuning);
 
 /*
+ * Shrink the chunk scratch to the current chunk_spectra (it is allocated at
+ * plan creation for the longest default chunk, up to 4 GiB, and only grows
+ * with vspec_plan_set_tuning). Synchronises the device, then frees and
+ * allocates; vspec_plan_info reports the new size. A caller whose calls are
+ * shorter sets chunk_spectra to its call length and trims; the batch
+ * autotuner does this for every bank. Errors: VSPEC_ERR_INVALID_ARG,
+ * VSPEC_ERR_OOM (the plan then has no scratch until a tuning grows it),
+ * VSPEC_ERR_CUDA.
+ */
+VSPEC_API vspec_status vspec_plan_trim_scratch(vspec_plan *plan);
+
+/*
  * Allocation-free variant of vspec_execute. The paper has no counterpart: it
  * is for callers that cannot call cudaMalloc, such as a host application that
  * owns every byte of device memory through its own pool, or a real-time

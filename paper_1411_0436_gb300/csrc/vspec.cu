@@ -1152,6 +1152,29 @@ vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
     return VSPEC_OK;
 }
 
+vspec_status vspec_plan_trim_scratch(vspec_plan *plan) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    vspec_plan *tk = plan->fused ? plan->assist : plan;
+    if (!tk || tk->fir_b || tk->sc_alloc <= tk->sc_max) return VSPEC_OK;
+    const size_t elem = tk->npol == 2 ? sizeof(float4) : sizeof(float2);
+    const size_t old_bytes = (size_t)tk->sc_alloc * tk->N * elem;
+    VSPEC_CUDA(cudaDeviceSynchronize());
+    cudaFree(tk->Z);
+    tk->Z = nullptr;
+    size_t tot = 0;
+    vspec_status st = dev_alloc(&tk->Z, (size_t)tk->sc_max * tk->N * elem, &tot);
+    if (st != VSPEC_OK) {
+        tk->sc_alloc = 0;
+        tk->scratch_bytes -= old_bytes;
+        if (tk != plan) plan->scratch_bytes -= old_bytes;
+        return st;
+    }
+    tk->scratch_bytes += tot - old_bytes;
+    if (tk != plan) plan->scratch_bytes += tot - old_bytes;
+    tk->sc_alloc = tk->sc_max;
+    return VSPEC_OK;
+}
+
 static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
                                 cudaStream_t st);
 

@@ -262,7 +262,11 @@ vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
             break;
         }
         cudaStreamSynchronize(st);
+        // a chunk longer than the bank's call is the same launch as one of the
+        // call's length: keep that, and trim the scratch to it
+        if (best_tuning.chunk_spectra > nspectra[i] && nspectra[i] > 0) best_tuning.chunk_spectra = nspectra[i];
         if (vspec_plan_set_tuning(best_plan, &best_tuning) != VSPEC_OK) result = VSPEC_ERR_CUDA;
+        if (result == VSPEC_OK && best_tuning.chunk_spectra > 0) result = vspec_plan_trim_scratch(best_plan);
         vspec_plan_destroy(batch->plans[i]);
         batch->plans[i] = best_plan;
         batch->flags[i] = best_flags;

@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_get_tuning.restype = i
         lib.vspec_plan_set_tuning.argtypes = [vp, ctypes.POINTER(VspecTuning)]
         lib.vspec_plan_set_tuning.restype = i
+        lib.vspec_plan_trim_scratch.argtypes = [vp]
+        lib.vspec_plan_trim_scratch.restype = i
         lib.vspec_plan_set_host_mode.argtypes = [vp, i, ctypes.c_size_t]
         lib.vspec_plan_set_host_mode.restype = i
         lib.vspec_status_string.argtypes = [i]
@@ -423,6 +425,12 @@ class Plan:
     def set_tuning(self, chunk_spectra: int, blocks_a: int, blocks_b: int, assist_permille: int,
                    two_kernel_from: int) -> None:
         vspec_plan_set_tuning(self.handle, chunk_spectra, blocks_a, blocks_b, assist_permille, two_kernel_from)
+
+    def trim_scratch(self) -> None:
+        """Shrink the chunk scratch to the current chunk length (vspec_plan_trim_scratch)."""
+        st = load().vspec_plan_trim_scratch(self.handle)
+        if st != OK:
+            raise VspecError(st, "vspec_plan_trim_scratch")
 
     def tune(self, **changes) -> dict:
         """Change some fields of the launch shape, keep the others; returns the new shape."""

@@ -317,6 +317,28 @@ def test_shaped_plans_match_oracle(oracle_mod, cfg, shapes):
         assert e.value.status in (vspec.ERR_UNSUPPORTED, vspec.ERR_INVALID_ARG)
 
 
+def test_trim_scratch_keeps_results(oracle_mod):
+    """A plan whose chunk is set to its call length and whose scratch is
+    trimmed holds less memory and gives the same spectrum."""
+    from paper_1411_0436_gb300.vspec import Plan
+    bank = Bank(131072, 8, 2, PFB, WIN_HANN, 37, rho=0.3)
+    x = workloads.generate(bank, 808)
+    o = run_oracle(oracle_mod, bank, x)
+    d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
+    with Plan(bank.nchan, 8, 2, PFB, WIN_HANN) as plan:
+        before, _ = plan.info()
+        plan.tune(chunk_spectra=bank.nspectra)
+        plan.trim_scratch()
+        after, _ = plan.info()
+        assert after < before and before - after >= (2048 - 37) * 131072 * 16
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        plan.execute(d_in, bank.nspectra, acc)
+        torch.cuda.synchronize()
+        assert_close(acc.cpu().numpy().astype(np.float64).reshape(-1, 4), o, what="trimmed scratch")
+        plan.tune(chunk_spectra=64)  # grows again
+        assert plan.info()[0] > after
+
+
 def test_plans_of_different_sizes_coexist():
     """A plan keeps working after another plan of the same kernels but smaller
     shared-memory needs was created (the kernels' shared-memory cap is shared)."""
