@@ -7,6 +7,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace vspec {
@@ -75,12 +76,36 @@ constexpr float kC8 = 0.70710678118654752440f;  // cos(pi/4)
 constexpr float kC16 = 0.92387953251128675613f; // cos(pi/8)
 constexpr float kS16 = 0.38268343236508977173f; // sin(pi/8)
 
+// A rotation by a compile-time constant c + i s on both polarisations at once:
+// (re + i im)(c + i s) = (re c - im s) + i (re s + im c) as four paired
+// instructions (the scalar form takes eight); the constant pairs are
+// immediates the compiler materialises.
+template <int QQ> __device__ __forceinline__ P2 rot_p2(P2 a) {
+    constexpr float c16[8] = {1.f, kC16, kC8, kS16, 0.f, -kS16, -kC8, -kC16};   // cos(q pi / 8)
+    constexpr float s16[8] = {0.f, -kS16, -kC8, -kC16, -1.f, -kC16, -kC8, -kS16};  // -sin(q pi / 8)
+    constexpr float c = c16[QQ], s = s16[QQ];
+    if constexpr (QQ == 2 || QQ == 6) {
+        // c = +-s: (re + i im)(c + i s) with |c| = |s| = 1/sqrt 2
+        if constexpr (QQ == 2) {  // c = kC8, s = -kC8: kC8 ((re + im) + i (im - re))
+            const float2 k = make_float2(kC8, kC8);
+            return P2{__fmul2_rn(__fadd2_rn(a.re, a.im), k), __fmul2_rn(sub2(a.im, a.re), k)};
+        } else {                  // c = s = -kC8: kC8 ((im - re) - i (re + im))
+            const float2 k = make_float2(kC8, kC8), nk = make_float2(-kC8, -kC8);
+            return P2{__fmul2_rn(sub2(a.im, a.re), k), __fmul2_rn(__fadd2_rn(a.re, a.im), nk)};
+        }
+    } else {
+        const float2 cc = make_float2(c, c), ss = make_float2(s, s), ns = make_float2(-s, -s);
+        return P2{__ffma2_rn(a.re, cc, __fmul2_rn(a.im, ns)), __ffma2_rn(a.im, cc, __fmul2_rn(a.re, ss))};
+    }
+}
+
 // W_R^q = exp(-2 pi i q / R) applied to a, for R in {8, 16}.
 template <int R, int Q, typename T> __device__ __forceinline__ T twiddle_const(T a) {
     static_assert(R == 8 || R == 16, "constant twiddles for R = 8, 16");
     constexpr int q = (R == 8) ? 2 * Q : Q;  // express as a 16th root
     if constexpr (q == 0) return a;
     else if constexpr (q == 4) return cmul_mi(a);
+    else if constexpr (std::is_same_v<T, P2>) return rot_p2<q>(a);
     else if constexpr (q == 2) return cmulc(a, kC8, -kC8);
     else if constexpr (q == 6) return cmulc(a, -kC8, -kC8);
     else if constexpr (q == 1) return cmulc(a, kC16, -kS16);
