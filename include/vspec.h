@@ -227,7 +227,8 @@ VSPEC_API vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int n
  *   h_out  host float[nchan * 4] (npol == 2) or float[nchan]: overwritten
  *          with the accumulated spectra of these nspectra spectra.
  * Two ways to bring the input over, chosen by vspec_plan_set_host_mode:
- *   staged  chunks of about 32 MiB of input (settable): a plan-owned copy stream fills
+ *   staged  chunks of input (by default a sixteenth of the first call's input,
+ *           within 32 .. 256 MiB; settable): a plan-owned copy stream fills
  *           one of two device staging buffers while a plan-owned compute
  *           stream channelizes the other;
  *   mapped  pinned host memory that the device can address (any cudaHostAlloc
@@ -236,8 +237,8 @@ VSPEC_API vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int n
  *           staging copy at all.
  * Auto maps when cudaPointerGetAttributes reports h_in as pinned host memory
  * with a device address, and stages otherwise. The default is staged: on
- * GB300 both ways run at the host link's rate (about 170 GB/s of input),
- * staged a little faster on short calls. All work starts
+ * GB300 both ways are bound by the host link (about 210 GB/s host to
+ * device), staged a little faster on short calls. All work starts
  * after the work already queued on `stream`, and `stream` waits for the final
  * copy, so the caller synchronises `stream` before reading h_out. The first
  * call on a plan allocates the staging buffers (two chunks of input plus one
@@ -256,7 +257,8 @@ VSPEC_API vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, 
 /*
  * Select how vspec_execute_host brings the input over (VSPEC_HOST_*), and the
  * staged mode's chunk: chunk_bytes of input per staging buffer, 1 MiB .. 4 GiB,
- * 0 for the default 32 MiB. Each chunk pays the per-call fixed costs and the
+ * 0 for automatic (a sixteenth of the first call's input, within 32 .. 256
+ * MiB, fixed from then on). Each chunk pays the per-call fixed costs and the
  * pipeline exposes one chunk's copy and one chunk's compute, so long calls gain
  * from longer chunks (measured on GB300 with 2.15 GB per call: 46 GHz at
  * 32 MiB, 49 GHz at 128 MiB; with 132 MB per call 32 MiB is best). A new

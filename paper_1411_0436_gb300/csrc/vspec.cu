@@ -181,7 +181,7 @@ struct vspec_plan {
     // host-input pipeline (vspec_execute_host), created on first use
     bool host_ready = false;
     int host_mode = VSPEC_HOST_STAGED;
-    size_t host_chunk_bytes = 32u << 20;
+    size_t host_chunk_bytes = 0;  // staged chunk of input bytes; 0: sized from the first call
     size_t host_bytes = 0;  // device memory of the host pipeline
     cudaStream_t copy_st = nullptr, comp_st = nullptr;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
@@ -1411,10 +1411,16 @@ vspec_status vspec_plan_kernel_stats(vspec_plan *plan, int kind, int reset, cons
 // Spectra per chunk of the host-input pipeline: about host_chunk_bytes of
 // input per staging buffer (at least 16 spectra), so copies and compute
 // overlap; the pipeline exposes one chunk's copy at the start and one
-// chunk's compute at the end.
-static int host_chunk_spectra(const vspec_plan *p) {
+// chunk's compute at the end. Automatic (host_chunk_bytes == 0): a sixteenth
+// of the first call's input, within 32 .. 256 MiB, so that the exposed ends
+// stay small while each chunk's fixed costs (launches, the P - 1 frames read
+// twice) are spread over more spectra.
+static int host_chunk_spectra(const vspec_plan *p, int nspectra) {
     const size_t per = (size_t)p->N * p->nsub * p->npol * 2;
-    return (int)std::max<size_t>(16, p->host_chunk_bytes / per);
+    size_t bytes = p->host_chunk_bytes;
+    if (bytes == 0)
+        bytes = std::min<size_t>(256u << 20, std::max<size_t>(32u << 20, (size_t)nspectra * per / 16));
+    return (int)std::max<size_t>(16, bytes / per);
 }
 
 vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspectra, float *h_out,
@@ -1426,7 +1432,7 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
     const size_t frame = (size_t)p->N * p->nsub * p->npol * 2;
     const size_t out_bytes = (size_t)p->nsub * p->N * (p->npol == 2 ? 4 : 1) * sizeof(float);
     if (!p->host_ready) {
-        p->stage_spectra = host_chunk_spectra(p);
+        p->stage_spectra = host_chunk_spectra(p, nspectra);
         const size_t sbytes = (size_t)(p->stage_spectra + Peff - 1) * frame;
         size_t tot = 0;
         vspec_status r;
@@ -1498,7 +1504,7 @@ vspec_status vspec_execute_host(vspec_plan *plan, const int8_t *h_in, int nspect
 vspec_status vspec_plan_set_host_mode(vspec_plan *plan, int mode, size_t chunk_bytes) {
     if (!plan || mode < VSPEC_HOST_AUTO || mode > VSPEC_HOST_MAPPED) return VSPEC_ERR_INVALID_ARG;
     if (chunk_bytes != 0 && (chunk_bytes < (1u << 20) || chunk_bytes > (1ull << 32))) return VSPEC_ERR_INVALID_ARG;
-    const size_t bytes = chunk_bytes ? chunk_bytes : (size_t)(32u << 20);
+    const size_t bytes = chunk_bytes;  // 0: automatic
     if (plan->host_ready && bytes != plan->host_chunk_bytes) {  // staging buffers are sized by the chunk
         VSPEC_CUDA(cudaDeviceSynchronize());
         release_host_pipeline(plan);
