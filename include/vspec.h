@@ -108,6 +108,15 @@ VSPEC_API vspec_status vspec_plan_create(vspec_plan **out, int nchan, int ntaps,
                                     accumulator through a plan-owned compensation buffer that
                                     vspec_dump clears; uses the two-kernel path (combinable with
                                     VSPEC_PLAN_TENSOR). With it, keep one accumulator per plan. */
+#define VSPEC_PLAN_RING 16u      /* the two-kernel path as one persistent launch per call
+                                    (cooperative: one CTA per SM): kernel-A and kernel-B work
+                                    handed out in dependency order, the four-step intermediate
+                                    in a ring of a few chunk slots (about 32 MiB each) that stays
+                                    in L2 instead of going through HBM. Dual-pol PFB of 5..8
+                                    taps with 2048-point rows (nchan 2^12..2^18); other plans
+                                    return VSPEC_ERR_UNSUPPORTED. Its waits are bounded (see
+                                    vspec_set_wait_limit; vspec_plan_check reports one that gave
+                                    up). Shape: vspec_plan_set_ring. */
 
 /*
  * vspec_plan_create with flags (a bitwise OR of VSPEC_PLAN_* values; 0 gives
@@ -158,13 +167,15 @@ VSPEC_API vspec_status vspec_plan_check(vspec_plan *plan);
 
 /*
  * Failure-path controls, for testing how callers handle a device-side wait
- * that gives up (no GPU fault is involved in either).
+ * that gives up (no GPU fault is involved in any of them).
  *
  * vspec_set_wait_limit sets, for every later launch in the process, how many
  * times a kernel polls before a bounded wait for its results gives up and
  * raises the plan's timeout flag (reported by vspec_plan_check or as
  * VSPEC_ERR_DEVICE_TIMEOUT by vspec_tc_dft16): polls >= 0 sets the limit (0
- * gives up at once), polls < 0 restores the default of 2^24. The wait that
+ * gives up at once), polls < 0 restores the default of 2^24 (a ring kernel
+ * sleeps about 100 ns between polls; when one of its waits gives up, the
+ * others return at once and the launch ends). The wait that
  * drains outstanding tensor-core work before a kernel frees its tensor
  * memory always keeps the default bound. Results computed under a wait that
  * gave up are incomplete and must be discarded.
@@ -191,6 +202,16 @@ VSPEC_API vspec_status vspec_set_wait_limit(long long polls);
  */
 VSPEC_API vspec_status vspec_debug_flags(unsigned *flags, int clear);
 VSPEC_API vspec_status vspec_plan_inject_timeout(vspec_plan *plan);
+
+/*
+ * For ring plans (VSPEC_PLAN_RING): the next launch starts the done counter of
+ * ring slot `slot` (counted from the call's first slot) one below zero, so
+ * that slot's kernel-B tickets wait for a kernel-A ticket that never comes:
+ * their bounded wait gives up, the launch ends without finishing the call,
+ * and vspec_plan_check reports VSPEC_ERR_DEVICE_TIMEOUT. Applies to one launch.
+ * Errors: VSPEC_ERR_INVALID_ARG, VSPEC_ERR_UNSUPPORTED (not a ring plan).
+ */
+VSPEC_API vspec_status vspec_plan_inject_stall(vspec_plan *plan, int slot);
 
 /* Release a plan and all device memory it owns. NULL is accepted. The caller
  * must make sure no work using the plan is still running on any stream. */
@@ -392,6 +413,29 @@ VSPEC_API vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tunin
  * VSPEC_ERR_CUDA.
  */
 VSPEC_API vspec_status vspec_plan_trim_scratch(vspec_plan *plan);
+
+/*
+ * Shape of a VSPEC_PLAN_RING plan's persistent launch (0 keeps a value):
+ *   slot_spectra  spectra per ring slot S (even, 2 .. 1024; default: the
+ *                 slot nearest 32 MiB of intermediate, 16 spectra at 2^17);
+ *   ring_slots    slots R of the ring (1 .. 16, at least lookahead; default 3);
+ *   lookahead     slots L of kernel-A work handed out ahead of kernel-B work
+ *                 (1 .. 15; default 2);
+ *   row_parts     kernel-B tickets V per row tile and slot (S / V even and at
+ *                 most 32; default S / 16, at least 1).
+ * Kernel-B tickets sum their spectra into partial-sum sets (c mod K) V + v,
+ * K = clamp(ceil(slots / 32), 2, sets / V), which a fold adds in order: the
+ * result does not depend on the order in which CTAs run (it is bitwise
+ * reproducible for a given shape and call length). Synchronises the device, then reallocates
+ * the ring (R S nchan 16 bytes) and the sets (up to 16 MiB); vspec_plan_info
+ * reports the size. Errors: VSPEC_ERR_INVALID_ARG (a value out of range),
+ * VSPEC_ERR_UNSUPPORTED (not a ring plan), VSPEC_ERR_OOM, VSPEC_ERR_CUDA.
+ * vspec_plan_get_ring reports the current shape (any pointer may be NULL).
+ */
+VSPEC_API vspec_status vspec_plan_set_ring(vspec_plan *plan, int slot_spectra, int ring_slots, int lookahead,
+                                           int row_parts);
+VSPEC_API vspec_status vspec_plan_get_ring(const vspec_plan *plan, int *slot_spectra, int *ring_slots,
+                                           int *lookahead, int *row_parts);
 
 /*
  * Allocation-free variant of vspec_execute. The paper has no counterpart: it

@@ -25,8 +25,13 @@
 #include "vspec_kernels_tc.cuh"
 #include "vspec_kernels_coltc.cuh"
 #include "vspec_kernels_tcfir.cuh"
+#include "vspec_ring.cuh"
 
 using vspec::Pass;
+
+// vspec_ring.cu
+const void *vspec_pick_kernel_ring(int N2, size_t *smem);
+cudaError_t vspec_ring_debug_flags(unsigned *flags, bool clear);
 
 namespace {
 
@@ -164,7 +169,18 @@ struct vspec_plan {
     unsigned char *dftop = nullptr;  // their DFT operand (fp16 hi, lo)
     bool kahan = false;        // compensated accumulation at every level
     void *partial_comp = nullptr, *out_comp = nullptr;
-    int *tc_status = nullptr;  // bounded-wait flag of the tensor-core kernel
+    int *tc_status = nullptr;  // bounded-wait flag of the tensor-core or ring kernel
+    // persistent ring form (VSPEC_PLAN_RING): Z holds ringR slots of ringS
+    // spectra, `partial` ring_sets partial-sum sets
+    bool ring = false;
+    int ringS = 0, ringR = 0, ringL = 0, ringV = 0;  // spectra per slot, slots, lookahead, B tickets per row
+    int ring_sets = 0;
+    int ring_discard = 1;        // drop consumed ring rows from L2 without a write-back
+    int ring_stall = -1;         // failure injection: the next launch's B tickets of this slot never start
+    int *ring_ctl = nullptr;     // ticket counter, abort flag, per-slot done counters
+    const void *kernelRing = nullptr;
+    size_t smemRing = 0;
+    int ring_grid = 0;           // CTAs of a ring launch (all resident)
     // sub-bands: input [time][nsub][pol][re, im], output [nsub][nchan]
     int nsub = 1;
     int sb_chunk = 0;          // spectra per de-interleaved chunk
@@ -305,8 +321,8 @@ cudaError_t take_event(vspec_plan *p, cudaEvent_t *ev) {
     return cudaEventCreate(ev);
 }
 
-// Launch one kernel on st (as clusters of `cluster` CTAs if cluster > 1); in
-// profiling mode bracket it with events.
+// Launch one kernel on st (as clusters of `cluster` CTAs if cluster > 1, as a
+// cooperative launch if cluster < 0); in profiling mode bracket it with events.
 vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 grid, dim3 block,
                     void **args, size_t smem, cudaStream_t st, int cluster = 0) {
     vspec_plan *o = p->owner ? p->owner : p;  // an assist plan records into its owner
@@ -334,6 +350,19 @@ vspec_status launch(vspec_plan *p, int kind, int spectra, const void *fn, dim3 g
         attr[1].val.priority = p->prio_high;
         cfg.attrs = attr;
         cfg.numAttrs = 2;
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+    } else if (cluster < 0) {
+        // cooperative: every CTA is resident at once (the ring kernel's CTAs wait on one another)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         e = cudaLaunchKernelExC(&cfg, fn, args);
     } else {
         e = cudaLaunchKernel(fn, grid, block, args, smem, st);
@@ -453,6 +482,7 @@ void free_plan(vspec_plan *p) {
     cudaFree(p->dftop);
     cudaFree(p->partial_comp);
     cudaFree(p->out_comp);
+    cudaFree(p->ring_ctl);
     delete p;
 }
 
@@ -480,10 +510,36 @@ constexpr size_t kScratchBudget = 4096ull << 20;
 constexpr size_t kScratchCap = 4096ull << 20;
 constexpr int kMaxChunkSpectra = 8192;  // small nchan: a default chunk long enough
 constexpr int kMaxWaves = 4;    // largest tuned launch, in waves of CTAs
+// Ring plans: slots of about kRingSlotBytes of intermediate, partial-sum sets
+// of up to kRingSetBytes, at most kRingSlotsPerLaunch slots per launch (the
+// per-slot done counters).
+constexpr size_t kRingSlotBytes = 32u << 20;
+constexpr size_t kRingSetBytes = 16u << 20;
+constexpr int kRingSlotsPerLaunch = 4096;
 
 // Partial-sum slots a kernel-B launch of n CTAs uses: a CTA's rank among the
 // CTAs that share a row tile stays below n / tiles + 2 (span_slot).
 int slots_for(const vspec_plan *p, int n) { return n / (p->N2 / p->RB) + 2; }
+
+// Partial-sum sets of a ring plan with V kernel-B tickets per row tile:
+// room for a set cycle K of at least 2 (up to 64 sets in kRingSetBytes).
+int ring_sets_for(const vspec_plan *p, int V) {
+    const size_t per = (size_t)p->N * sizeof(float4);
+    return std::max(2 * V, (int)std::min<size_t>(64, kRingSetBytes / per));
+}
+
+// Default ring shape: slots of about kRingSlotBytes (an even spectrum count),
+// kernel-B tickets of 16 spectra (8 per 256-thread group), three slots with
+// kernel-A work two slots ahead.
+void ring_default_shape(vspec_plan *p) {
+    const size_t per = (size_t)p->N * sizeof(float4);
+    const int S = (int)std::min<size_t>(1024, std::max<size_t>(2, kRingSlotBytes / per)) & ~1;
+    p->ringS = S;
+    p->ringV = std::max(1, S / 16);
+    p->ringR = 3;
+    p->ringL = 2;
+    p->ring_sets = ring_sets_for(p, p->ringV);
+}
 constexpr int kRowElems = 2048;  // target row-DFT elements per kernel-B CTA
 
 // Fused one-pass plan: dual-pol, 2048..32768 channels, 8-tap PFB or direct.
@@ -803,8 +859,34 @@ vspec_status build_plan(vspec_plan *p) {
         p->fold2048 = N2 >= 16 && !p->kahan;
     }
 
+    // the persistent ring form: the register-column kernel A and the paired
+    // 2048-point row kernel as tickets of one launch
+    if (p->flags & VSPEC_PLAN_RING) {
+        if (!colreg || std::strcmp(p->formB, "row2048") != 0 || p->npol != 2 || p->kahan || p->tc || p->fir_b) {
+            g_last_error = "the ring form needs dual-pol PFB of 5..8 taps with 2048-point rows (nchan 2^12..2^18)";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        p->kernelRing = vspec_pick_kernel_ring(N2, &p->smemRing);
+        if (!p->kernelRing) {
+            g_last_error = "no ring kernel instance for this column length";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        p->ring = true;
+    }
+
     VSPEC_CUDA(cudaGetDevice(&p->device));
     VSPEC_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (p->ring) {
+        int coop = 0, occ = 0;
+        VSPEC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device));
+        VSPEC_CUDA(raise_smem_cap(p->kernelRing, p->smemRing));
+        VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p->kernelRing, 512, p->smemRing));
+        if (!coop || occ < 1) {
+            g_last_error = "the ring kernel needs cooperative launches and one resident CTA per SM";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        p->ring_grid = p->num_sms * occ;
+    }
     VSPEC_CUDA(raise_smem_cap(p->kernelA, p->smemA));
     VSPEC_CUDA(raise_smem_cap(p->kernelB, p->smemB));
     VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->occA, p->kernelA, p->TA, p->smemA));
@@ -832,9 +914,16 @@ vspec_status build_plan(vspec_plan *p) {
     if ((st = dev_alloc((void **)&p->invA, sizeof(int) * (size_t)N2, &tot))) return st;
     if ((st = dev_alloc((void **)&p->invB, sizeof(int) * (size_t)N1, &tot))) return st;
     p->sc_alloc = p->fir_b ? 0 : p->sc_max;
+    if (p->ring) {  // the ring and its partial-sum sets instead of the chunk scratch
+        ring_default_shape(p);
+        p->sc_alloc = p->sc_max = p->sc_cap = p->ringR * p->ringS;
+        p->slots_cap = p->ring_sets;
+        if ((st = dev_alloc((void **)&p->ring_ctl, sizeof(int) * (2 + 2 * (size_t)kRingSlotsPerLaunch), &tot)))
+            return st;
+    }
     if ((st = dev_alloc(&p->Z, (size_t)std::max(1, p->sc_alloc) * N * elem, &tot))) return st;
     if ((st = dev_alloc(&p->partial, (size_t)p->slots_cap * N * accel, &tot))) return st;
-    if (p->tc || p->tc_cols) {
+    if (p->tc || p->tc_cols || p->ring) {
         if ((st = dev_alloc((void **)&p->tc_status, sizeof(int), &tot))) return st;
         VSPEC_CUDA(cudaMemset(p->tc_status, 0, sizeof(int)));
     }
@@ -998,7 +1087,8 @@ vspec_status vspec_plan_create_shaped(vspec_plan **out, int nchan, int ntaps, in
     p->npol = npol;
     p->mode = mode;
     p->window = window;
-    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN | VSPEC_PLAN_TENSOR_INT8)) {
+    if (flags & ~(unsigned)(VSPEC_PLAN_TWO_KERNEL | VSPEC_PLAN_TENSOR | VSPEC_PLAN_KAHAN | VSPEC_PLAN_TENSOR_INT8 |
+                            VSPEC_PLAN_RING)) {
         delete p;
         *out = nullptr;
         return VSPEC_ERR_INVALID_ARG;
@@ -1007,6 +1097,7 @@ vspec_status vspec_plan_create_shaped(vspec_plan **out, int nchan, int ntaps, in
     p->req_n2 = col_len;
     p->req_cols = tile_cols;
     if (col_len || tile_cols) p->flags |= VSPEC_PLAN_TWO_KERNEL;  // a shape is a two-kernel shape
+    if (flags & VSPEC_PLAN_RING) p->flags |= VSPEC_PLAN_TWO_KERNEL;  // the ring runs kernels A and B
     vspec_status st = build_plan(p);
     if (st == VSPEC_OK && p->fused) st = setup_assist(p);
     if (st != VSPEC_OK) {
@@ -1060,7 +1151,7 @@ vspec_status vspec_plan_info(const vspec_plan *plan, size_t *scratch_bytes, int 
         // (a fused plan reports the two-kernel path it switches to on long calls)
         const vspec_plan *tk = !plan->fused ? plan : plan->two_kernel_from < INT_MAX ? plan->assist : nullptr;
         const size_t zb = tk ? (size_t)tk->sc_max * tk->N * (tk->npol == 2 ? sizeof(float4) : sizeof(float2)) : 0;
-        *hbm_passes = (tk && !tk->fir_b && zb > (size_t)l2 / 2) ? 2 : 1;
+        *hbm_passes = (tk && !tk->fir_b && !tk->ring && zb > (size_t)l2 / 2) ? 2 : 1;
     }
     return VSPEC_OK;
 }
@@ -1073,6 +1164,9 @@ vspec_status vspec_plan_describe(const vspec_plan *plan, char *buf, size_t len) 
                         " chunk=" + std::to_string(t->sc_max);
         if (t->fir_b) d += " fir-in-B";
         if (t->kahan) d += " kahan";
+        if (t->ring)
+            d += " ring S=" + std::to_string(t->ringS) + " R=" + std::to_string(t->ringR) + " L=" +
+                 std::to_string(t->ringL) + " V=" + std::to_string(t->ringV);
         return d;
     };
     std::string d;
@@ -1113,6 +1207,10 @@ vspec_status vspec_plan_get_tuning(const vspec_plan *plan, vspec_tuning *current
 
 vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
     if (!plan || !t) return VSPEC_ERR_INVALID_ARG;
+    if (plan->ring) {
+        g_last_error = "a ring plan is shaped by vspec_plan_set_ring";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
     vspec_tuning lim{};
     vspec_plan_get_tuning(plan, nullptr, &lim);
     vspec_plan *tk = plan->fused ? plan->assist : plan;
@@ -1149,6 +1247,65 @@ vspec_status vspec_plan_set_tuning(vspec_plan *plan, const vspec_tuning *t) {
         plan->assist_permille = t->assist_permille;
         plan->two_kernel_from = t->two_kernel_from;
     }
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_set_ring(vspec_plan *plan, int slot_spectra, int ring_slots, int lookahead, int row_parts) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (!plan->ring) {
+        g_last_error = "not a ring plan (VSPEC_PLAN_RING)";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    if (slot_spectra < 0 || ring_slots < 0 || lookahead < 0 || row_parts < 0) return VSPEC_ERR_INVALID_ARG;
+    const int S = slot_spectra ? slot_spectra : plan->ringS;
+    const int R = ring_slots ? ring_slots : plan->ringR;
+    const int L = lookahead ? lookahead : plan->ringL;
+    const int V = row_parts ? row_parts : (slot_spectra ? std::max(1, S / 16) : plan->ringV);
+    if (S < 2 || S > 1024 || (S & 1) || R < 1 || R > 16 || L < 1 || L > 15 || R < L || V < 1 || S % V ||
+        ((S / V) & 1) || S / V > 32) {
+        g_last_error = "ring shape out of range";
+        return VSPEC_ERR_INVALID_ARG;
+    }
+    const size_t elem = sizeof(float4);
+    const int sets = ring_sets_for(plan, V);
+    VSPEC_CUDA(cudaDeviceSynchronize());
+    cudaFree(plan->Z);
+    cudaFree(plan->partial);
+    plan->Z = plan->partial = nullptr;
+    plan->scratch_bytes -= (size_t)plan->sc_alloc * plan->N * elem + (size_t)plan->slots_cap * plan->N * elem;
+    plan->sc_alloc = plan->sc_max = plan->sc_cap = 0;
+    plan->slots_cap = 0;
+    size_t tot = 0;
+    vspec_status st = dev_alloc(&plan->Z, (size_t)R * S * plan->N * elem, &tot);
+    if (st == VSPEC_OK) st = dev_alloc(&plan->partial, (size_t)sets * plan->N * elem, &tot);
+    if (st != VSPEC_OK) {  // the plan keeps no ring: a later call fails until a shape fits
+        cudaFree(plan->Z);
+        plan->Z = nullptr;
+        plan->ringS = 0;
+        return st;
+    }
+    plan->scratch_bytes += tot;
+    plan->ringS = S;
+    plan->ringR = R;
+    plan->ringL = L;
+    plan->ringV = V;
+    plan->ring_sets = sets;
+    plan->sc_alloc = plan->sc_max = plan->sc_cap = R * S;
+    plan->slots_cap = sets;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_get_ring(const vspec_plan *plan, int *slot_spectra, int *ring_slots, int *lookahead,
+                                 int *row_parts) {
+    if (!plan) return VSPEC_ERR_INVALID_ARG;
+    if (!plan->ring) {
+        g_last_error = "not a ring plan (VSPEC_PLAN_RING)";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    if (slot_spectra) *slot_spectra = plan->ringS;
+    if (ring_slots) *ring_slots = plan->ringR;
+    if (lookahead) *lookahead = plan->ringL;
+    if (row_parts) *row_parts = plan->ringV;
     return VSPEC_OK;
 }
 
@@ -1262,27 +1419,11 @@ static vspec_status run_fused(vspec_plan *p, const int8_t *d_in, int nspectra, f
 // detection (kernel B) through the chunk scratch (in L2 only if a tuned
 // chunk is short enough), then the fold of the partial sums into d_accum,
 // after `before_fold` if it is given.
-static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
-                                   cudaStream_t st, cudaEvent_t before_fold) {
-    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
-    // one full wave of CTAs per launch unless tuned; the work is split evenly
-    // over them (block_span), so every SM stays busy to the end of a launch
-    const int nA = p->blocks_a > 0 ? p->blocks_a : p->num_sms * p->occA;
-    const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
-    // equal chunks of at most sc_max spectra (no short ragged last chunk)
-    const int nchunks = (nspectra + p->sc_max - 1) / p->sc_max;
-    const int sc_full = (nspectra + nchunks - 1) / nchunks;
-    // slots of the largest kernel-B launch (no more CTAs than items)
-    const int tilesB = p->N2 / p->RB;
-    int slots = slots_for(p, (int)std::min<long long>(nB, (long long)tilesB * sc_full));
-    // a one-row transform in one launch: block k is the only writer of slot k
-    // and stores it, so nothing needs zeroing and the fold reads those slots
-    const bool store = p->fir_b && !p->kahan && !p->tc && nchunks == 1;
-    if (store) slots = (int)std::min<long long>(nB, (long long)tilesB * sc_full);
-    if (!store) VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
-    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
-
-    vspec::ColParams ca{};
+// Kernel A's and kernel B's parameters for one call (the per-launch fields,
+// chunk start and length, slots and the store flag, are the caller's).
+static void make_params(const vspec_plan *p, const int8_t *d_in, int nspectra, vspec::ColParams &ca,
+                        vspec::RowParams &cb) {
+    ca = vspec::ColParams{};
     ca.in = d_in;
     ca.coef = p->coef;
     ca.twA = p->twA;
@@ -1306,7 +1447,7 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     ca.wait_limit = g_wait_limit.load();
     ca.bterms = p->bterms;
 
-    vspec::RowParams cb{};
+    cb = vspec::RowParams{};
     cb.Z = p->Z;
     cb.partial = p->partial;
     cb.partial_comp = p->partial_comp;
@@ -1320,12 +1461,37 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     cb.npass = (int)p->passB.size();
     for (int i = 0; i < cb.npass; i++) cb.pass[i] = p->passB[i];
     cb.tiles = p->N2 / p->RB;
-    cb.slots = slots;
     cb.in = d_in;
     cb.coef = p->coef;
     cb.P = p->P;
-    cb.store = store;
     cb.nframes = ca.nframes;
+}
+
+static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
+                                   cudaStream_t st, cudaEvent_t before_fold) {
+    const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
+    // one full wave of CTAs per launch unless tuned; the work is split evenly
+    // over them (block_span), so every SM stays busy to the end of a launch
+    const int nA = p->blocks_a > 0 ? p->blocks_a : p->num_sms * p->occA;
+    const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
+    // equal chunks of at most sc_max spectra (no short ragged last chunk)
+    const int nchunks = (nspectra + p->sc_max - 1) / p->sc_max;
+    const int sc_full = (nspectra + nchunks - 1) / nchunks;
+    // slots of the largest kernel-B launch (no more CTAs than items)
+    const int tilesB = p->N2 / p->RB;
+    int slots = slots_for(p, (int)std::min<long long>(nB, (long long)tilesB * sc_full));
+    // a one-row transform in one launch: block k is the only writer of slot k
+    // and stores it, so nothing needs zeroing and the fold reads those slots
+    const bool store = p->fir_b && !p->kahan && !p->tc && nchunks == 1;
+    if (store) slots = (int)std::min<long long>(nB, (long long)tilesB * sc_full);
+    if (!store) VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * p->N * accel, st));
+    if (p->kahan) VSPEC_CUDA(cudaMemsetAsync(p->partial_comp, 0, (size_t)slots * p->N * accel, st));
+
+    vspec::ColParams ca;
+    vspec::RowParams cb;
+    make_params(p, d_in, nspectra, ca, cb);
+    cb.slots = slots;
+    cb.store = store;
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);
@@ -1352,8 +1518,55 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     return launch_fold(p, slots, d_accum, nspectra, st);
 }
 
+// The persistent ring form: one cooperative launch per kRingSlotsPerLaunch
+// slots (each with its done counters zeroed first), then the fold of the
+// partial-sum sets in set order.
+static vspec_status run_ring(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum, cudaStream_t st) {
+    if (p->ringS == 0 || !p->Z || !p->partial) {
+        g_last_error = "the ring plan has no ring (a reshape failed)";
+        return VSPEC_ERR_OOM;
+    }
+    const int S = p->ringS, V = p->ringV;
+    const long long nslot_all = ((long long)nspectra + S - 1) / S;
+    // set cycle: about 32 slot sums per set, at least 2 (B(c) then waits for B(c - K) only)
+    const int K = (int)std::min<long long>(p->ring_sets / V, std::max<long long>(2, (nslot_all + 31) / 32));
+    vspec::RingParams q{};
+    make_params(p, d_in, nspectra, q.a, q.b);
+    q.ring = p->Z;
+    q.sets = p->partial;
+    q.status = p->tc_status;
+    q.wait_limit = g_wait_limit.load();
+    q.S = S;
+    q.R = p->ringR;
+    q.L = p->ringL;
+    q.V = V;
+    q.K = K;
+    q.tilesA = p->N1 / p->C;
+    q.tilesB = p->N2;
+    q.discard = p->ring_discard;
+    for (long long c0 = 0; c0 < nslot_all; c0 += kRingSlotsPerLaunch) {
+        q.nslot = (int)std::min<long long>(kRingSlotsPerLaunch, nslot_all - c0);
+        q.c0 = (int)c0;
+        q.s0 = c0 * S;
+        q.nspectra = (int)std::min<long long>((long long)nspectra - c0 * S, (long long)q.nslot * S);
+        q.ctl = p->ring_ctl;
+        VSPEC_CUDA(cudaMemsetAsync(p->ring_ctl, 0, sizeof(int) * (2 + 2 * (size_t)q.nslot), st));
+        if (p->ring_stall >= 0 && p->ring_stall < q.nslot) {
+            // failure injection: one more A ticket than slot ring_stall has, so its B tickets' wait gives up
+            VSPEC_CUDA(cudaMemsetAsync(p->ring_ctl + 2 + p->ring_stall, 0xff, sizeof(int), st));  // -1
+            p->ring_stall = -1;
+        }
+        void *args[] = {&q};
+        vspec_status r = launch(p, 3, q.nspectra, p->kernelRing, dim3(p->ring_grid), dim3(512), args, p->smemRing,
+                                st, -1);
+        if (r != VSPEC_OK) return r;
+    }
+    return launch_fold(p, (int)std::min<long long>(K, nslot_all) * V, d_accum, nspectra, st);
+}
+
 static vspec_status execute_one(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
                                 cudaStream_t st) {
+    if (p->ring) return run_ring(p, d_in, nspectra, d_accum, st);
     if (!p->fused) return run_two_kernel(p, d_in, nspectra, d_accum, st, nullptr);
     if (p->assist && nspectra >= p->two_kernel_from)
         return run_two_kernel(p->assist, d_in, nspectra, d_accum, st, nullptr);
@@ -1534,6 +1747,9 @@ vspec_status vspec_debug_flags(unsigned *flags, int clear) {
         const unsigned zero = 0;
         VSPEC_CUDA(cudaMemcpyToSymbol(vspec::g_debug_flags, &zero, sizeof(unsigned)));
     }
+    unsigned ring_flags = 0;  // the ring kernels' own word
+    VSPEC_CUDA(vspec_ring_debug_flags(&ring_flags, clear != 0));
+    *flags |= ring_flags;
     return VSPEC_OK;
 #else
     (void)flags;
@@ -1557,6 +1773,16 @@ vspec_status vspec_plan_inject_timeout(vspec_plan *plan) {
     }
     const int one = 1;
     VSPEC_CUDA(cudaMemcpy(plan->tc_status, &one, sizeof(int), cudaMemcpyHostToDevice));
+    return VSPEC_OK;
+}
+
+vspec_status vspec_plan_inject_stall(vspec_plan *plan, int slot) {
+    if (!plan || slot < 0) return VSPEC_ERR_INVALID_ARG;
+    if (!plan->ring) {
+        g_last_error = "only ring plans wait on other CTAs' work";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    plan->ring_stall = slot;
     return VSPEC_OK;
 }
 

@@ -41,7 +41,11 @@ constexpr int kMaxPasses = 6;
 //   bit 3: tile index out of range
 enum : unsigned { kDbgScratch = 1u, kDbgInput = 2u, kDbgSlot = 4u, kDbgTile = 8u };
 #ifdef VSPEC_DEBUG
+#ifdef VSPEC_NO_PLAN_TABLES
+static __device__ unsigned int g_debug_flags;  // this translation unit's own word
+#else
 __device__ unsigned int g_debug_flags;
+#endif
 __device__ __forceinline__ bool dbg_ok(bool cond, unsigned bit) {
     if (!cond) atomicOr(&g_debug_flags, bit);
     return cond;
@@ -477,11 +481,16 @@ struct ColReg {
     static_assert(B1 * PTS == SPB * C * (N2 / R1) && B2 * PTS == SPB * C * R1, "whole butterflies per thread");
 };
 
-template <int N2, int R1 = N2>
-__global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__ ColParams p) {
+// Tile x of the register-column kernel A over spectra s_beg .. s_end - 1 of
+// a chunk: spectrum s of the chunk is absolute spectrum s0 + s and goes to
+// Zc[s] (the chunk holds sc spectra). All PTS threads of the CTA take part;
+// the function ends with a barrier. twc: load the first-pass twiddles (they
+// stay in shared memory for later tiles of the same launch).
+template <int N2, int R1>
+__device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long long s0, int sc, int x, int s_beg,
+                                            int s_end, unsigned char *smem_raw, bool load_twc) {
     using G = ColReg<N2, R1>;
     constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int SS = G::SS;
     P2 *data = reinterpret_cast<P2 *>(smem_raw);                       // [SPB][SS]
     float2 *tws = reinterpret_cast<float2 *>(data + SPB * SS);         // [N2][C], at twi(pos, c)
@@ -491,16 +500,11 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
     const int t = threadIdx.x;                                         // point n2 * C + c
     const int D = PT - p.P;                                            // leading zero taps
     // first-pass twiddles W_N2^(j q) (ordered before use by the loop's barriers)
-    for (int e = t; e < G::TWC; e += blockDim.x) twc[e] = __ldg(p.twA + p.pass[0].off + e);
-    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
-    for (long long f = sp.lo; f < sp.hi;) {
-        const long long base = f / p.sc * p.sc;  // first item of this super-tile
-        const int x = (int)(f / p.sc) * sp.G + sp.r;
-        const int s_beg = (int)(f - base);
-        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
-        f = base + s_end;
+    if (load_twc)
+        for (int e = t; e < G::TWC; e += PTS) twc[e] = __ldg(p.twA + p.pass[0].off + e);
+    {
         const int n1_0 = x * C;
-        for (int e = t; e < PTS; e += blockDim.x)  // W_N^(n1 k2), k2 = pos
+        for (int e = t; e < PTS; e += PTS)  // W_N^(n1 k2), k2 = pos
             tws[G::twi(e / C, e % C)] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
 
         const long long n_pt = n1_0 + (t % C) + (long long)p.N1 * (t / C);
@@ -511,7 +515,7 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
         for (int k = 0; k < PT; k++) cfs[k * PTS + t] = k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) : 0.f;
         // slot (s - s_beg + k) % PT of the window holds frame s + k - D
         P2 win[PT];
-        const long long sabs = p.s0 + s_beg;
+        const long long sabs = s0 + s_beg;
 #pragma unroll
         for (int k = 0; k < PT - 1; k++) {
             long long fr = sabs - D + k;
@@ -522,10 +526,10 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
         auto stage = [&](int sb, int buf) {
             const int nbb = min(SPB, s_end - sb);
             constexpr int per_row = C / 4, per_frame = PTS / 4;
-            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
+            for (int e = t; e < nbb * per_frame; e += PTS) {
                 const int u = e / per_frame, r = e % per_frame;
                 const int n2 = r / per_row, ch = r % per_row;
-                const long long fr = p.s0 + sb + u + p.P - 1;
+                const long long fr = s0 + sb + u + p.P - 1;
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
                                       (long long)p.N1 * n2 + ch * 4;
                 uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
@@ -571,8 +575,8 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
 #pragma unroll
                         for (int q = 0; q < N2; q++) v[q] = data[sb * SS + q * C + c];
                         Dft<N2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
-                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
                         for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(q, c)]);
@@ -609,9 +613,9 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
 #pragma unroll
                         for (int q = 0; q < R2; q++) v[q] = d[q * C];
                         Dft<R2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
-                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
+                        if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
                         for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[G::twi(b * R2 + q, c)]);
                     }
@@ -619,6 +623,22 @@ __global__ void __launch_bounds__(512) fir_colreg_kernel(const __grid_constant__
             }
         }
         __syncthreads();  // the column passes are done with the twiddle tile
+    }
+}
+
+template <int N2, int R1 = N2>
+__global__ void __launch_bounds__(512, 1) fir_colreg_kernel(const __grid_constant__ ColParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
+    bool first = true;
+    for (long long f = sp.lo; f < sp.hi;) {
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        colreg_tile<N2, R1>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first);
+        first = false;
     }
 }
 
@@ -1144,11 +1164,34 @@ __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 constexpr int kRow2048Stride = 2048 + 2048 / 8;
 constexpr int kRow2048Run = 16;  // spectra per register run (a multiple of 2)
 
+// Barriers of a 2048-point row worker of 256 threads: the whole CTA (the
+// ordinary kernel), or one of the two 256-thread groups of a 512-thread CTA
+// (named barriers 1 + g for the group, 3 + 2 g + half for its halves).
+struct RowGrpCta {
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void sync_half(int half) const {
+        if (half) asm volatile("bar.sync 2, 128;" ::: "memory");
+        else asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+};
+struct RowGrp2 {
+    int g;  // threads 256 g .. 256 g + 255
+    __device__ __forceinline__ int tid() const { return threadIdx.x & 255; }
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, 256;" :: "r"(1 + g) : "memory"); }
+    __device__ __forceinline__ void sync_half(int half) const {
+        asm volatile("bar.sync %0, 128;" :: "r"(3 + 2 * g + half) : "memory");
+    }
+};
+
 // ZSPLIT: the scratch elements hold (X.re, X.im, Y.re, Y.im) (the tensor-core
 // column kernel's order) instead of the packed (X.re, Y.re, X.im, Y.im).
-template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
-__device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<NPOL>::T *row, int x,
-                                              int s, int ht, int half) {
+// Zc: the chunk's scratch (sc spectra); CG: read it through L2 only (ld.cg;
+// the scratch of the persistent form is rewritten while CTAs run).
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool CG, typename GRP>
+__device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc, int sc,
+                                              typename Elem<NPOL>::T *row, int x, int s, int ht, int half,
+                                              GRP grp) {
     using T = typename Elem<NPOL>::T;
     // pass 1: block length 2048, butterfly j = ht over positions j + 128 q
     {
@@ -1158,16 +1201,25 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] = fir_sample<NPOL>(p, p.s0 + s, ht + 128 * q);
         } else if constexpr (ZSPLIT) {
-            const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
+            const float4 *zr = reinterpret_cast<const float4 *>(Zc) + (size_t)s * p.N + (size_t)x * 2048;
 #pragma unroll
             for (int q = 0; q < 16; q++) {
                 const float4 e = zr[ht + 128 * q];
                 v[q] = make_p2(e.x, e.y, e.z, e.w);
             }
-        } else if (dbg_ok(s < p.sc && (x + 1) * 2048 <= p.N, kDbgScratch | kDbgTile)) {
-            const T *zr = reinterpret_cast<const T *>(p.Z) + (size_t)s * p.N + (size_t)x * 2048;
+        } else if (dbg_ok(s < sc && (x + 1) * 2048 <= p.N, kDbgScratch | kDbgTile)) {
+            const T *zr = reinterpret_cast<const T *>(Zc) + (size_t)s * p.N + (size_t)x * 2048;
+            if constexpr (CG && NPOL == 2) {
+                const float4 *z4 = reinterpret_cast<const float4 *>(zr);
 #pragma unroll
-            for (int q = 0; q < 16; q++) v[q] = zr[ht + 128 * q];
+                for (int q = 0; q < 16; q++) {
+                    const float4 e = __ldcg(z4 + ht + 128 * q);
+                    v[q] = P2{make_float2(e.x, e.y), make_float2(e.z, e.w)};
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; q++) v[q] = zr[ht + 128 * q];
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] = T{};
@@ -1179,8 +1231,7 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, typename Elem<
 #pragma unroll
         for (int q = 0; q < 16; q++) row[pad8(ht + 128 * q)] = v[q];
     }
-    if (half) asm volatile("bar.sync 2, 128;" ::: "memory");
-    else asm volatile("bar.sync 1, 128;" ::: "memory");
+    grp.sync_half(half);
     // pass 2: block length 128, unit b = ht / 8, butterfly j = ht % 8
     {
         const Pass ps = p.pass[1];
@@ -1219,15 +1270,80 @@ __device__ __forceinline__ void row2048_last(const typename Elem<NPOL>::T *row, 
     }
 }
 
-template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
-__global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __grid_constant__ RowParams p) {
+// Row tile x (2048 positions) over spectra s_beg .. s_end - 1 of a chunk
+// (scratch Zc, sc spectra), detected and summed in registers; each register
+// run of kRow2048Run spectra, and the rest at the end, is added into the
+// worker's slot row `part` (its entries 8 t .. 8 t + 7; pcomp: their Kahan
+// compensation). first: the slot's first write this call stores instead of
+// adding (with an empty range, zeros). part == nullptr: no slot (a failed
+// debug check). smem: the worker's two rows.
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool CG, typename GRP>
+__device__ __forceinline__ void row2048_seg(const RowParams &p, const void *Zc, int sc, int x, int s_beg, int s_end,
+                                            typename Elem<NPOL>::Acc *part, typename Elem<NPOL>::Acc *pcomp,
+                                            bool first, unsigned char *smem, GRP grp) {
     using T = typename Elem<NPOL>::T;
     using A = typename Elem<NPOL>::Acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *rows = reinterpret_cast<T *>(smem_raw);  // two rows, pad8 layout
-    const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127;
+    T *rows = reinterpret_cast<T *>(smem);  // two rows, pad8 layout
+    const int tid = grp.tid(), half = tid >> 7, ht = tid & 127;
     T *own = rows + half * kRow2048Stride;
 
+    A acc[8], comp[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else acc[q] = 0.f;
+        comp[q] = acc[q];
+    }
+    // add the registers into the slot; `store`: the slot's first write this call
+    auto flush = [&](bool store) {
+        if (!part) return;
+        A *pt = part + 8 * tid;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if constexpr (KAHAN) {
+                A *pc = pcomp + 8 * tid;
+                A a = pt[q], c = pc[q];
+                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
+                else kahan_add(a, c, acc[q] - comp[q]);
+                pt[q] = a;
+                pc[q] = c;
+            } else if (store) {
+                pt[q] = acc[q];
+            } else {
+                // a reduction performed in L2: no wait for the slot's old
+                // value. Only this thread adds to these entries, in program
+                // order, so the sums are the same as a load-add-store's.
+                atomicAdd(pt + q, acc[q]);
+            }
+        }
+    };
+    for (int s = s_beg; s < s_end; s += 2) {
+        const bool two = s + 1 < s_end;
+        if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR, ZSPLIT, CG>(p, Zc, sc, own, x, s + half, ht, half, grp);
+        grp.sync();
+        row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
+        if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
+        if constexpr (!KAHAN) {
+            // end of a register run with more spectra to come: into the slot
+            if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2 && s + 2 < s_end) {
+                flush(first);
+                first = false;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    else acc[q] = 0.f;
+                }
+            }
+        }
+        grp.sync();  // both rows are free for the next pair
+    }
+    flush(first);
+}
+
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
+__global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __grid_constant__ RowParams p) {
+    using A = typename Elem<NPOL>::Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);  // row tile
@@ -1235,61 +1351,13 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
-
-        A acc[8], comp[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            else acc[q] = 0.f;
-            comp[q] = acc[q];
-        }
-        // add the registers into this block's slot (thread t holds positions
-        // 8t .. 8t+7 of row tile x); `store`: the slot's first write this call
-        auto flush = [&](bool store) {
-            if (!dbg_ok(span_slot(p.tiles, p.sc, x) < p.slots && (x + 1) * 2048 <= p.N, kDbgSlot)) return;
-            const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
-            A *part = reinterpret_cast<A *>(p.partial) + so;
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                if constexpr (KAHAN) {
-                    A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
-                    A a = part[q], c = pc[q];
-                    if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
-                    else kahan_add(a, c, acc[q] - comp[q]);
-                    part[q] = a;
-                    pc[q] = c;
-                } else if (store) {
-                    part[q] = acc[q];
-                } else {
-                    // a reduction performed in L2: no wait for the slot's old
-                    // value. Only this thread adds to these entries, in program
-                    // order, so the sums are the same as a load-add-store's.
-                    atomicAdd(part + q, acc[q]);
-                }
-            }
-        };
-        bool first = p.store != 0;
-        for (int s = s_beg; s < s_end; s += 2) {
-            const bool two = s + 1 < s_end;
-            if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR, ZSPLIT>(p, own, x, s + half, ht, half);
-            __syncthreads();
-            row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
-            if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
-            if constexpr (!KAHAN) {
-                // end of a register run with more spectra to come: into the slot
-                if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2 && s + 2 < s_end) {
-                    flush(first);
-                    first = false;
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        else acc[q] = 0.f;
-                    }
-                }
-            }
-            __syncthreads();  // both rows are free for the next pair
-        }
-        flush(first);
+        const int slot = span_slot(p.tiles, p.sc, x);
+        const bool ok = dbg_ok(slot < p.slots && (x + 1) * 2048 <= p.N, kDbgSlot);
+        const size_t so = (size_t)slot * p.N + (size_t)x * 2048;
+        A *part = ok ? reinterpret_cast<A *>(p.partial) + so : nullptr;
+        A *pcomp = KAHAN ? reinterpret_cast<A *>(p.partial_comp) + so : nullptr;
+        row2048_seg<NPOL, KAHAN, FIR, ZSPLIT, false>(p, p.Z, p.sc, x, s_beg, s_end, part, pcomp, p.store != 0,
+                                                      smem_raw, RowGrpCta{});
     }
 }
 
@@ -1554,7 +1622,9 @@ __global__ void __launch_bounds__(256) reduce_kahan_kernel(const void *partial, 
 }
 
 // ------------------------------------------------------ plan-time tables ---
-// All plan tables are computed in FP64 and rounded once to FP32.
+// All plan tables are computed in FP64 and rounded once to FP32. (Defined in
+// one translation unit: the others define VSPEC_NO_PLAN_TABLES.)
+#ifndef VSPEC_NO_PLAN_TABLES
 
 constexpr double kPi = 3.14159265358979323846;
 
@@ -1601,5 +1671,6 @@ __global__ void gen_twz_kernel(float2 *twZ, int N, int N1, int N2, const int *di
     const long long m = ((long long)n1 * digrevA[pos]) % N;
     twZ[e] = root_of_unity(m, N);
 }
+#endif  // VSPEC_NO_PLAN_TABLES
 
 }  // namespace vspec

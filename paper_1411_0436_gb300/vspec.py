@@ -30,6 +30,7 @@ PLAN_TWO_KERNEL = 1  # force the general two-kernel path
 PLAN_TENSOR = 2      # first 2048-point row pass on the tensor cores
 PLAN_KAHAN = 4       # compensated accumulation
 PLAN_TENSOR_INT8 = 8  # pre-filter + column DFT as one tensor-core product on the int8 input
+PLAN_RING = 16       # one persistent launch per call, the intermediate in an L2-sized ring
 
 _lib = None
 
@@ -138,6 +139,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_plan_set_tuning.restype = i
         lib.vspec_plan_trim_scratch.argtypes = [vp]
         lib.vspec_plan_trim_scratch.restype = i
+        lib.vspec_plan_set_ring.argtypes = [vp, i, i, i, i]
+        lib.vspec_plan_set_ring.restype = i
+        lib.vspec_plan_get_ring.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
+        lib.vspec_plan_get_ring.restype = i
+        lib.vspec_plan_inject_stall.argtypes = [vp, i]
+        lib.vspec_plan_inject_stall.restype = i
         lib.vspec_plan_set_host_mode.argtypes = [vp, i, ctypes.c_size_t]
         lib.vspec_plan_set_host_mode.restype = i
         lib.vspec_status_string.argtypes = [i]
@@ -326,6 +333,27 @@ def vspec_plan_inject_timeout(plan: int) -> None:
         raise VspecError(st, "vspec_plan_inject_timeout")
 
 
+def vspec_plan_set_ring(plan: int, slot_spectra: int = 0, ring_slots: int = 0, lookahead: int = 0,
+                        row_parts: int = 0) -> None:
+    st = load().vspec_plan_set_ring(plan, slot_spectra, ring_slots, lookahead, row_parts)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_set_ring")
+
+
+def vspec_plan_get_ring(plan: int) -> dict:
+    v = [ctypes.c_int() for _ in range(4)]
+    st = load().vspec_plan_get_ring(plan, *[ctypes.byref(x) for x in v])
+    if st != OK:
+        raise VspecError(st, "vspec_plan_get_ring")
+    return dict(zip(("slot_spectra", "ring_slots", "lookahead", "row_parts"), (int(x.value) for x in v)))
+
+
+def vspec_plan_inject_stall(plan: int, slot: int) -> None:
+    st = load().vspec_plan_inject_stall(plan, slot)
+    if st != OK:
+        raise VspecError(st, "vspec_plan_inject_stall")
+
+
 def vspec_tc_dft16(d_x, d_y, batch: int, terms: int = 3, stream=None) -> None:
     st = load().vspec_tc_dft16(_addr(d_x), _addr(d_y), batch, terms, _stream(stream))
     if st != OK:
@@ -406,6 +434,18 @@ class Plan:
     def inject_timeout(self) -> None:
         """Raise the plan's timeout flag from the host (failure-path tests)."""
         vspec_plan_inject_timeout(self.handle)
+
+    def set_ring(self, slot_spectra: int = 0, ring_slots: int = 0, lookahead: int = 0, row_parts: int = 0) -> None:
+        """Shape of a ring plan's persistent launch (vspec_plan_set_ring; 0 keeps a value)."""
+        vspec_plan_set_ring(self.handle, slot_spectra, ring_slots, lookahead, row_parts)
+
+    def ring(self) -> dict:
+        """The ring plan's shape (vspec_plan_get_ring)."""
+        return vspec_plan_get_ring(self.handle)
+
+    def inject_stall(self, slot: int) -> None:
+        """Make the next ring launch's kernel-B tickets of `slot` wait for nothing (failure-path tests)."""
+        vspec_plan_inject_stall(self.handle, slot)
 
     def check(self) -> None:
         """Raise if a bounded device-side wait of this plan expired."""
