@@ -429,9 +429,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         vsteps = max(3, min(args.steps, 50))
         from paper_1411_0436_gb300.vspec import NEVER
         from paper_1411_0436_gb300.vspec import PLAN_KAHAN
-        from paper_1411_0436_gb300.vspec import PLAN_TENSOR_INT8
+        from paper_1411_0436_gb300.vspec import PLAN_RING, PLAN_TENSOR_INT8
         cands = [("tensor_core", PLAN_TENSOR, None), ("tensor_core_int8", PLAN_TENSOR_INT8, None),
-                 ("fp32_two_kernel", PLAN_TWO_KERNEL, None), ("fp32_kahan", PLAN_KAHAN, None)]
+                 ("fp32_two_kernel", PLAN_TWO_KERNEL, None), ("fp32_kahan", PLAN_KAHAN, None),
+                 ("fp32_ring", PLAN_RING, None)]
         if n <= 32768:  # the one-pass cluster kernel on every call length
             cands.append(("fp32_fused_cluster", 0, {"two_kernel_from": NEVER, "assist_permille": 0}))
         for key, flags, tuning in cands:
@@ -521,6 +522,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                             variants["fp32_default"]["value"])
         variants["tc_int8_speedup_over_fp32"] = (variants["tensor_core_int8"]["value"] /
                                                  variants["fp32_default"]["value"])
+        variants["ring_speedup_over_fp32"] = (variants["fp32_ring"]["value"] /
+                                              variants["fp32_default"]["value"])
 
     plan.close()
     # the batched multi-beam workload (rank 0 at N=1), as an extra key

@@ -1186,13 +1186,15 @@ struct RowGrp2 {
 
 // ZSPLIT: the scratch elements hold (X.re, X.im, Y.re, Y.im) (the tensor-core
 // column kernel's order) instead of the packed (X.re, Y.re, X.im, Y.im).
-// Zc: the chunk's scratch (sc spectra); CG: read it through L2 only (ld.cg;
-// the scratch of the persistent form is rewritten while CTAs run).
-template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool CG, typename GRP>
-__device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc, int sc,
+// RING: the chunk's scratch is Zc (sc spectra), read through L2 only (ld.cg:
+// the persistent form rewrites it while CTAs run); otherwise p.Z and p.sc.
+template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool RING, typename GRP>
+__device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc_ring, int sc_ring,
                                               typename Elem<NPOL>::T *row, int x, int s, int ht, int half,
                                               GRP grp) {
     using T = typename Elem<NPOL>::T;
+    const void *Zc = RING ? Zc_ring : p.Z;
+    const int sc = RING ? sc_ring : p.sc;
     // pass 1: block length 2048, butterfly j = ht over positions j + 128 q
     {
         const Pass ps = p.pass[0];
@@ -1209,7 +1211,7 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc
             }
         } else if (dbg_ok(s < sc && (x + 1) * 2048 <= p.N, kDbgScratch | kDbgTile)) {
             const T *zr = reinterpret_cast<const T *>(Zc) + (size_t)s * p.N + (size_t)x * 2048;
-            if constexpr (CG && NPOL == 2) {
+            if constexpr (RING && NPOL == 2) {
                 const float4 *z4 = reinterpret_cast<const float4 *>(zr);
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
@@ -1270,80 +1272,15 @@ __device__ __forceinline__ void row2048_last(const typename Elem<NPOL>::T *row, 
     }
 }
 
-// Row tile x (2048 positions) over spectra s_beg .. s_end - 1 of a chunk
-// (scratch Zc, sc spectra), detected and summed in registers; each register
-// run of kRow2048Run spectra, and the rest at the end, is added into the
-// worker's slot row `part` (its entries 8 t .. 8 t + 7; pcomp: their Kahan
-// compensation). first: the slot's first write this call stores instead of
-// adding (with an empty range, zeros). part == nullptr: no slot (a failed
-// debug check). smem: the worker's two rows.
-template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool CG, typename GRP>
-__device__ __forceinline__ void row2048_seg(const RowParams &p, const void *Zc, int sc, int x, int s_beg, int s_end,
-                                            typename Elem<NPOL>::Acc *part, typename Elem<NPOL>::Acc *pcomp,
-                                            bool first, unsigned char *smem, GRP grp) {
-    using T = typename Elem<NPOL>::T;
-    using A = typename Elem<NPOL>::Acc;
-    T *rows = reinterpret_cast<T *>(smem);  // two rows, pad8 layout
-    const int tid = grp.tid(), half = tid >> 7, ht = tid & 127;
-    T *own = rows + half * kRow2048Stride;
-
-    A acc[8], comp[8];
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-        if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else acc[q] = 0.f;
-        comp[q] = acc[q];
-    }
-    // add the registers into the slot; `store`: the slot's first write this call
-    auto flush = [&](bool store) {
-        if (!part) return;
-        A *pt = part + 8 * tid;
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if constexpr (KAHAN) {
-                A *pc = pcomp + 8 * tid;
-                A a = pt[q], c = pc[q];
-                if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
-                else kahan_add(a, c, acc[q] - comp[q]);
-                pt[q] = a;
-                pc[q] = c;
-            } else if (store) {
-                pt[q] = acc[q];
-            } else {
-                // a reduction performed in L2: no wait for the slot's old
-                // value. Only this thread adds to these entries, in program
-                // order, so the sums are the same as a load-add-store's.
-                atomicAdd(pt + q, acc[q]);
-            }
-        }
-    };
-    for (int s = s_beg; s < s_end; s += 2) {
-        const bool two = s + 1 < s_end;
-        if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR, ZSPLIT, CG>(p, Zc, sc, own, x, s + half, ht, half, grp);
-        grp.sync();
-        row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
-        if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
-        if constexpr (!KAHAN) {
-            // end of a register run with more spectra to come: into the slot
-            if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2 && s + 2 < s_end) {
-                flush(first);
-                first = false;
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    else acc[q] = 0.f;
-                }
-            }
-        }
-        grp.sync();  // both rows are free for the next pair
-    }
-    flush(first);
-}
-
 template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT = false>
 __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __grid_constant__ RowParams p) {
+    using T = typename Elem<NPOL>::T;
     using A = typename Elem<NPOL>::Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw);  // two rows, pad8 layout
+    const int tid = threadIdx.x, half = tid >> 7, ht = tid & 127;
+    T *own = rows + half * kRow2048Stride;
+
     const Span sp = block_span(p.tiles, p.sc);
     for (long long f = sp.lo; f < sp.hi;) {
         const int x = (int)(f / p.sc);  // row tile
@@ -1351,13 +1288,61 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
-        const int slot = span_slot(p.tiles, p.sc, x);
-        const bool ok = dbg_ok(slot < p.slots && (x + 1) * 2048 <= p.N, kDbgSlot);
-        const size_t so = (size_t)slot * p.N + (size_t)x * 2048;
-        A *part = ok ? reinterpret_cast<A *>(p.partial) + so : nullptr;
-        A *pcomp = KAHAN ? reinterpret_cast<A *>(p.partial_comp) + so : nullptr;
-        row2048_seg<NPOL, KAHAN, FIR, ZSPLIT, false>(p, p.Z, p.sc, x, s_beg, s_end, part, pcomp, p.store != 0,
-                                                      smem_raw, RowGrpCta{});
+
+        A acc[8], comp[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else acc[q] = 0.f;
+            comp[q] = acc[q];
+        }
+        // add the registers into this block's slot (thread t holds positions
+        // 8t .. 8t+7 of row tile x); `store`: the slot's first write this call
+        auto flush = [&](bool store) {
+            if (!dbg_ok(span_slot(p.tiles, p.sc, x) < p.slots && (x + 1) * 2048 <= p.N, kDbgSlot)) return;
+            const size_t so = (size_t)span_slot(p.tiles, p.sc, x) * p.N + (size_t)x * 2048 + 8 * tid;
+            A *part = reinterpret_cast<A *>(p.partial) + so;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if constexpr (KAHAN) {
+                    A *pc = reinterpret_cast<A *>(p.partial_comp) + so;
+                    A a = part[q], c = pc[q];
+                    if constexpr (NPOL == 2) kahan_add(a, c, sub4(acc[q], comp[q]));
+                    else kahan_add(a, c, acc[q] - comp[q]);
+                    part[q] = a;
+                    pc[q] = c;
+                } else if (store) {
+                    part[q] = acc[q];
+                } else {
+                    // a reduction performed in L2: no wait for the slot's old
+                    // value. Only this thread adds to these entries, in program
+                    // order, so the sums are the same as a load-add-store's.
+                    atomicAdd(part + q, acc[q]);
+                }
+            }
+        };
+        bool first = p.store != 0;
+        for (int s = s_beg; s < s_end; s += 2) {
+            const bool two = s + 1 < s_end;
+            if (half == 0 || two) row2048_first<NPOL, KAHAN, FIR, ZSPLIT, false>(p, nullptr, 0, own, x, s + half, ht, half, RowGrpCta{});
+            __syncthreads();
+            row2048_last<NPOL, KAHAN>(rows, tid, acc, comp);
+            if (two) row2048_last<NPOL, KAHAN>(rows + kRow2048Stride, tid, acc, comp);
+            if constexpr (!KAHAN) {
+                // end of a register run with more spectra to come: into the slot
+                if (((s - s_beg) & (kRow2048Run - 1)) == kRow2048Run - 2 && s + 2 < s_end) {
+                    flush(first);
+                    first = false;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        if constexpr (NPOL == 2) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        else acc[q] = 0.f;
+                    }
+                }
+            }
+            __syncthreads();  // both rows are free for the next pair
+        }
+        flush(first);
     }
 }
 

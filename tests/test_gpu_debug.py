@@ -36,18 +36,21 @@ vspec.vspec_debug_flags(clear=True)
 # (nchan, taps, npol, mode, window, spectra, flags): register-column kernel A
 # for 2..64-point columns, direct-mode columns, the tap-gather form, the
 # general kernel A (single-pol), one-row transforms with the FIR in kernel B,
-# the general row kernel, compensated plans, several chunks
+# the general row kernel, compensated plans, several chunks, the persistent ring form
 shapes = [(4096, 8, 2, PFB, WIN_HANN, 19, 0), (32768, 8, 2, PFB, WIN_HANN, 67, 1),
           (131072, 8, 2, PFB, WIN_HANN, 5, 0), (524288, 1, 2, DIRECT, WIN_RECT, 3, 0),
           (1 << 19, 8, 2, PFB, WIN_HANN, 3, 0), (1024, 8, 1, PFB, WIN_HANN, 64, 0),
           (8192, 2, 1, PFB, WIN_HANN, 7, 0), (65536, 4, 1, PFB, WIN_HANN, 6, 0),
-          (2048, 5, 2, PFB, WIN_RECT, 40, 4), (16384, 1, 2, DIRECT, WIN_HANN, 9, 4)]
+          (2048, 5, 2, PFB, WIN_RECT, 40, 4), (16384, 1, 2, DIRECT, WIN_HANN, 9, 4),
+          (131072, 8, 2, PFB, WIN_HANN, 37, 16), (32768, 8, 2, PFB, WIN_HANN, 131, 16)]
 out = []
 for n, p, npol, mode, win, s, flags in shapes:
     bank = Bank(n, p, npol, mode, win, s, rho=0.3 if npol == 2 else 0.0, tones=(Tone(30.0, n * 0.3 + 0.4, (0,)),))
     x = workloads.generate(bank, 900 + n)
     with vspec.Plan(n, p, npol, mode, win, flags) as plan:
-        if n == 32768:
+        if n == 32768 and flags & 16:
+            plan.set_ring(slot_spectra=4, ring_slots=2, lookahead=1)  # many slots through a small ring
+        elif n == 32768:
             plan.tune(chunk_spectra=16)  # several chunks
         d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda()
         acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
