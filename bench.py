@@ -593,21 +593,36 @@ def measure_batch(steps: int, warmup: int) -> dict:
     batch_shapes = [dict(batch.bank_tuning(i)[1], col_len=batch.bank_shape(i)[0], tile_cols=batch.bank_shape(i)[1])
                     for i in range(len(flags))]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    for _ in range(warmup):
-        flush.fill_(1)
-        batch.execute(d_in, ns, accs, stream)
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    for i in range(steps):
-        flush.fill_(i & 0xFF)
-        starts[i].record(stream)
-        batch.execute(d_in, ns, accs, stream)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
+    def timed() -> float:
+        for _ in range(warmup):
+            flush.fill_(1)
+            batch.execute(d_in, ns, accs, stream)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+            batch.execute(d_in, ns, accs, stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
+    total_ms = timed()
     samples = sum(b.nspectra * b.nchan for b in banks)
     value = steps * samples / (total_ms * 1e-3) / 1e9
+    # the same banks as one persistent launch (every bank's kernels as tickets of one kernel)
+    persistent = None
+    try:
+        batch.set_persistent(True)
+        pms = timed()
+        batch.check()
+        persistent = {"value": steps * samples / (pms * 1e-3) / 1e9, "unit": "GHz", "ms_per_step": pms / steps,
+                      "what": "one cooperative launch: kernel-A tiles, rows and folds of all banks as tickets"}
+        batch.set_persistent(False)
+    except Exception as e:  # a bank the persistent kernel has no body for
+        persistent = {"unavailable": str(e)}
     in_bytes = sum(x.nbytes for x in xs)
     peak, peak_kind = _peaks()
     achieved = steps * sum(b.nbytes + 2 * b.nchan * 16 for b in banks) / (total_ms * 1e-3) / 1e9
@@ -616,6 +631,7 @@ def measure_batch(steps: int, warmup: int) -> dict:
             "workload": "8 dual-pol banks 1024..524288 channels, PFB-8/direct alternating, "
                         "2048..64 spectra, one CUDA-graph launch per step",
             "input_bytes": int(in_bytes), "bank_flags": flags, "bank_shapes": batch_shapes,
+            "persistent": persistent,
             "path_roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                               "peak_source": peak_kind}}
 
@@ -631,7 +647,7 @@ def run_batch(args):
         "config": {"workload": r["workload"], "input_bytes": r["input_bytes"], "bank_flags": r["bank_flags"],
                    "bank_shapes": r["bank_shapes"],
                    "l2": "flushed between steps (256 MiB write outside the timed interval)"},
-        "path_roofline": r["path_roofline"],
+        "path_roofline": r["path_roofline"], "persistent": r["persistent"],
     }), flush=True)
 
 

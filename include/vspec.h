@@ -515,8 +515,11 @@ VSPEC_API vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *con
  * (vspec_plan_create_shaped). Each in several launch shapes
  * (vspec_plan_set_tuning): its default, chunks a half and a quarter as long,
  * kernel B over two waves of CTAs, and for a plan that can switch between the
- * fused and the two-kernel path, each path alone. Clears every d_accum[i]
- * afterwards and synchronises `stream`. vspec_batch_bank_flags reports the
+ * fused and the two-kernel path, each path alone. Then the whole batch: its
+ * graph of per-bank kernels against the persistent launch over all banks
+ * (vspec_batch_set_persistent; banks whose chosen plan has no ticket body run
+ * their two-kernel plan in it), keeping the faster (vspec_batch_get_persistent
+ * reports which). Clears every d_accum[i] afterwards and synchronises `stream`. vspec_batch_bank_flags reports the
  * VSPEC_PLAN_* flags of the plan chosen for bank `bank`;
  * vspec_batch_bank_tuning also its launch shape and vspec_batch_bank_shape its
  * split and tile width (vspec_plan_get_shape); output pointers may be NULL.
@@ -528,6 +531,41 @@ VSPEC_API vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank
 VSPEC_API vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigned *flags,
                                                vspec_tuning *tuning);
 VSPEC_API vspec_status vspec_batch_bank_shape(const vspec_batch *batch, int bank, int *col_len, int *tile_cols);
+
+/*
+ * Persistent mode: the batch's graph holds one cooperative launch (one
+ * 512-thread CTA per SM) instead of every bank's kernels. That kernel runs
+ * all banks' work as tickets in three phases, handed out in order by an
+ * atomic counter: kernel-A tiles of every bank (the register-column forms,
+ * into the bank's chunk scratch), then row tickets (16 spectra of one
+ * 2048-point row, or of a one-row transform with its pre-filter), then fold
+ * tickets (512 channels: the row tickets' sums, added in order and
+ * compensated, into the caller's accumulator). A bank's row tickets wait
+ * (bounded, vspec_set_wait_limit) until its kernel-A tickets are done, its
+ * folds until its row tickets are; results do not depend on which CTA ran
+ * what. A bank with a fused one-pass plan runs the two-kernel plan that the
+ * fused plan owns; enabling the mode gives every other bank whose plan has no
+ * ticket body its VSPEC_PLAN_TWO_KERNEL plan. Banks must be dual-pol: PFB of 5..8 taps up to
+ * 2^18 channels, direct mode up to 2^19 channels, or one-row transforms
+ * (up to 1024 channels with at most 8 taps, or 2048); at most 16 banks, each
+ * call no longer than its plan's chunk scratch (the autotuner's choice, or
+ * the default chunk). Errors of vspec_batch_set_persistent:
+ * VSPEC_ERR_INVALID_ARG, VSPEC_ERR_UNSUPPORTED (a bank or the bank count;
+ * the reason in vspec_last_error), VSPEC_ERR_OOM; of vspec_batch_execute in
+ * this mode also VSPEC_ERR_UNSUPPORTED (a call too long for its plan).
+ * enable = 0 returns to per-bank kernels. vspec_batch_autotune chooses the
+ * mode by timing both.
+ *
+ * vspec_batch_check synchronises and reports (once) whether a wait of the
+ * persistent kernel gave up (VSPEC_ERR_DEVICE_TIMEOUT; the call's results are
+ * incomplete). vspec_batch_inject_stall makes the next persistent execute
+ * start bank `bank`'s kernel-A done counter one below zero, so that its row
+ * tickets' wait gives up (failure-path tests; no GPU fault is involved).
+ */
+VSPEC_API vspec_status vspec_batch_set_persistent(vspec_batch *batch, int enable);
+VSPEC_API vspec_status vspec_batch_get_persistent(const vspec_batch *batch, int *enabled);
+VSPEC_API vspec_status vspec_batch_check(vspec_batch *batch);
+VSPEC_API vspec_status vspec_batch_inject_stall(vspec_batch *batch, int bank);
 
 /*
  * Batched 16-point DFTs on the tensor cores (tcgen05.mma, bf16 operands,

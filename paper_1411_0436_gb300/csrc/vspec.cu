@@ -26,12 +26,19 @@
 #include "vspec_kernels_coltc.cuh"
 #include "vspec_kernels_tcfir.cuh"
 #include "vspec_ring.cuh"
+#include "vspec_bp.cuh"
+#include "vspec_internal.h"
 
 using vspec::Pass;
 
 // vspec_ring.cu
 const void *vspec_pick_kernel_ring(int N2, size_t *smem);
 cudaError_t vspec_ring_debug_flags(unsigned *flags, bool clear);
+// vspec_bp.cu
+const void *vspec_bp_kernel();
+size_t vspec_bp_smem_a(int form, int N2);
+size_t vspec_bp_smem_b(int form, int N1, int P);
+cudaError_t vspec_bp_debug_flags(unsigned *flags, bool clear);
 
 namespace {
 
@@ -1564,6 +1571,133 @@ static vspec_status run_ring(vspec_plan *p, const int8_t *d_in, int nspectra, fl
     return launch_fold(p, (int)std::min<long long>(K, nslot_all) * V, d_accum, nspectra, st);
 }
 
+}  // extern "C"
+
+// ------------------------------------------------ persistent multi-bank --
+// (C++ linkage: declared in vspec_internal.h for vspec_batch.cu)
+// The plan whose forms a bank of the persistent launch runs: a fused plan's
+// own two-kernel plan (which its long calls run anyway), else the plan.
+static vspec_plan *bp_plan(vspec_plan *p) { return p->fused && p->assist ? p->assist : p; }
+
+// Ticket body of a plan in the persistent multi-bank launch, -1 if none.
+static int bp_form(const vspec_plan *p0, const char **why) {
+    const vspec_plan *p = bp_plan(const_cast<vspec_plan *>(p0));
+    const char *w = nullptr;
+    int f = -1;
+    if (p->npol != 2 || p->fused || p->kahan || p->tc || p->tc_cols || p->ring || p0->nsub != 1)
+        w = "needs a dual-pol two-kernel FP32 plan (VSPEC_PLAN_TWO_KERNEL) without sub-bands";
+    else if (p->fir_b && p->N == 2048 && std::strcmp(p->formB, "row2048") == 0)
+        f = vspec::kBpRow2048Fir;
+    else if (p->fir_b && p->N <= 1024 && p->P <= 8 && p->RB == 1)
+        f = vspec::kBpRowFir;
+    else if (!p->fir_b && std::strcmp(p->formB, "row2048") == 0 && std::strcmp(p->formA, "colreg") == 0)
+        f = vspec::kBpColreg;
+    else if (!p->fir_b && std::strcmp(p->formB, "row2048") == 0 && std::strcmp(p->formA, "coldir") == 0)
+        f = vspec::kBpColdir;
+    else
+        w = "needs the register-column kernel A with 2048-point rows (PFB of 5..8 taps up to 2^18 channels, "
+            "direct mode up to 2^19) or a one-row transform (up to 1024 channels with at most 8 taps, or 2048)";
+    if (why) *why = w;
+    return f;
+}
+
+void vspec_set_last_error(const char *what) { g_last_error = what ? what : ""; }
+
+vspec_status vspec_bp_supported(const vspec_plan *p, const char **why) {
+    if (!p) return VSPEC_ERR_INVALID_ARG;
+    return bp_form(p, why) >= 0 ? VSPEC_OK : VSPEC_ERR_UNSUPPORTED;
+}
+
+vspec_status vspec_bp_execute(vspec_plan *const *plans, int n, const int8_t *const *d_in, const int *nspectra,
+                              float *const *d_accum, int *ctl, int *status, int stall_bank, cudaStream_t st) {
+    using namespace vspec;
+    if (!plans || !d_in || !nspectra || !d_accum || !ctl || n < 1) return VSPEC_ERR_INVALID_ARG;
+    if (n > kBpMaxBanks) {
+        g_last_error = "the persistent launch holds at most 16 banks";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    static BpParams q;  // about 10 KB of kernel parameters (callers are serialised per batch)
+    static std::mutex q_mutex;
+    std::lock_guard<std::mutex> lock(q_mutex);
+    q = BpParams{};
+    size_t smem = 0;
+    q.nbanks = n;
+    for (int i = 0; i < n; i++) {
+        vspec_plan *p = plans[i] ? bp_plan(plans[i]) : nullptr;
+        const char *why = nullptr;
+        const int form = p ? bp_form(p, &why) : -1;
+        if (form < 0) {
+            g_last_error = why ? why : "missing plan";
+            return p ? VSPEC_ERR_UNSUPPORTED : VSPEC_ERR_INVALID_ARG;
+        }
+        const int ns = nspectra[i];
+        if (ns < 0 || !d_in[i] || !d_accum[i]) return VSPEC_ERR_INVALID_ARG;
+        if (!aligned16(d_in[i]) || !aligned16(d_accum[i])) return VSPEC_ERR_ALIGNMENT;
+        const bool rowonly = form == kBpRowFir || form == kBpRow2048Fir;
+        if (!rowonly && ns > p->sc_alloc) {
+            g_last_error = "a bank's call is longer than its plan's chunk scratch (tune chunk_spectra to the call)";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        BpBank &b = q.banks[i];
+        make_params(p, d_in[i], ns, b.a, b.b);
+        b.a.s0 = 0;
+        b.a.sc = ns;
+        b.b.s0 = 0;
+        b.b.sc = ns;
+        b.Z = p->Z;
+        b.sets = reinterpret_cast<float4 *>(p->partial);
+        b.acc = reinterpret_cast<float4 *>(d_accum[i]);
+        b.invA = p->invA;
+        b.invB = p->invB;
+        b.form = form;
+        b.N2 = p->N2;
+        b.nspectra = ns;
+        // tickets of about 20 us of work: 64 spectra of a 512-point PFB tile,
+        // 16 of a 2048-point direct tile, 16 of a row (8 per group; up to 32
+        // where the sets would not fit the plan's partial sums)
+        b.TA = form == kBpColreg ? 64 : 16;
+        b.TB = 16;
+        while ((ns + b.TB - 1) / b.TB > p->slots_cap && b.TB < 32) b.TB += 2;
+        if ((ns + b.TB - 1) / b.TB > p->slots_cap) {
+            g_last_error = "a bank's call needs more partial-sum sets than its plan holds";
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        b.tilesA = rowonly ? 0 : p->N1 / p->C;
+        b.tilesB = rowonly ? 1 : p->N2;
+        b.nA = ns > 0 ? b.tilesA * ((ns + b.TA - 1) / b.TA) : 0;
+        b.nB = ns > 0 ? b.tilesB * ((ns + b.TB - 1) / b.TB) : 0;
+        b.nF = ns > 0 ? (p->N + 511) / 512 : 0;
+        if (!rowonly) smem = std::max(smem, vspec_bp_smem_a(form, p->N2));
+        smem = std::max(smem, vspec_bp_smem_b(form, p->N1, p->P));
+        q.offA[i + 1] = q.offA[i] + b.nA;
+        q.offB[i + 1] = q.offB[i] + b.nB;
+        q.offF[i + 1] = q.offF[i] + b.nF;
+    }
+    q.ctl = ctl;
+    q.status = status;
+    q.wait_limit = g_wait_limit.load();
+    vspec_plan *p0 = bp_plan(plans[0]);
+    const void *fn = vspec_bp_kernel();
+    static std::once_flag raised;
+    static cudaError_t raise_err = cudaSuccess;
+    std::call_once(raised, [&] { raise_err = raise_smem_cap(fn, 232448 - 64); });
+    VSPEC_CUDA(raise_err);
+    int occ = 0;
+    VSPEC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, smem));
+    if (occ < 1) {
+        g_last_error = "the multi-bank kernel does not fit on an SM";
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    VSPEC_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * (2 + 2 * (size_t)n), st));
+    if (stall_bank >= 0 && stall_bank < n) VSPEC_CUDA(cudaMemsetAsync(ctl + 2 + 2 * stall_bank, 0xff, sizeof(int), st));
+    int spectra = 0;
+    for (int i = 0; i < n; i++) spectra += nspectra[i];
+    void *args[] = {&q};
+    return launch(p0, 3, spectra, fn, dim3(p0->num_sms * occ), dim3(512), args, smem, st, -1);
+}
+
+extern "C" {
+
 static vspec_status execute_one(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
                                 cudaStream_t st) {
     if (p->ring) return run_ring(p, d_in, nspectra, d_accum, st);
@@ -1747,9 +1881,10 @@ vspec_status vspec_debug_flags(unsigned *flags, int clear) {
         const unsigned zero = 0;
         VSPEC_CUDA(cudaMemcpyToSymbol(vspec::g_debug_flags, &zero, sizeof(unsigned)));
     }
-    unsigned ring_flags = 0;  // the ring kernels' own word
+    unsigned ring_flags = 0, bp_flags = 0;  // the ring and multi-bank kernels' own words
     VSPEC_CUDA(vspec_ring_debug_flags(&ring_flags, clear != 0));
-    *flags |= ring_flags;
+    VSPEC_CUDA(vspec_bp_debug_flags(&bp_flags, clear != 0));
+    *flags |= ring_flags | bp_flags;
     return VSPEC_OK;
 #else
     (void)flags;

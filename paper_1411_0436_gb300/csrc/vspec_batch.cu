@@ -5,7 +5,10 @@
 // (§5). A batch owns one plan per bank; vspec_batch_execute records every
 // bank's kernels into one CUDA graph, one forked stream branch per bank so
 // that banks of different sizes run concurrently, and replays it with a
-// single graph launch. Built only on the public C ABI.
+// single graph launch. In persistent mode (vspec_batch_set_persistent) the
+// graph instead holds one cooperative launch that runs every bank's kernels
+// as tickets of one kernel (vspec_bp.cuh, through vspec_internal.h); the rest
+// is built on the public C ABI.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +18,7 @@
 #include <vector>
 
 #include "vspec.h"
+#include "vspec_internal.h"
 
 struct vspec_batch {
     int nbanks = 0;
@@ -27,6 +31,10 @@ struct vspec_batch {
     cudaStream_t capture = nullptr;
     cudaEvent_t forked = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // persistent mode: control words and timeout flag of the multi-bank launch
+    bool persistent = false;
+    int *bp_ctl = nullptr, *bp_status = nullptr;
+    int stall_bank = -1;
     // arguments the graph was captured with
     std::vector<const int8_t *> g_in;
     std::vector<int> g_ns;
@@ -43,6 +51,8 @@ void destroy_batch(vspec_batch *b) {
     for (cudaEvent_t e : b->joined) cudaEventDestroy(e);
     if (b->forked) cudaEventDestroy(b->forked);
     if (b->capture) cudaStreamDestroy(b->capture);
+    cudaFree(b->bp_ctl);
+    cudaFree(b->bp_status);
     delete b;
 }
 
@@ -59,8 +69,12 @@ vspec_status capture_graph(vspec_batch *b, const int8_t *const *d_in, const int 
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return VSPEC_ERR_CUDA;
     vspec_status st = VSPEC_OK;
+    if (b->persistent) {  // one cooperative launch over every bank
+        st = vspec_bp_execute(b->plans.data(), b->nbanks, d_in, nspectra, d_accum, b->bp_ctl, b->bp_status, -1,
+                              b->capture);
+    }
     e = cudaEventRecord(b->forked, b->capture);
-    for (int i = 0; i < b->nbanks && e == cudaSuccess && st == VSPEC_OK; i++) {
+    for (int i = 0; i < b->nbanks && e == cudaSuccess && st == VSPEC_OK && !b->persistent; i++) {
         e = cudaStreamWaitEvent(b->branch[i], b->forked, 0);
         if (e != cudaSuccess) break;
         st = vspec_execute(b->plans[i], d_in[i], nspectra[i], d_accum[i], (void *)b->branch[i]);
@@ -152,6 +166,12 @@ vspec_status vspec_batch_execute(vspec_batch *batch, const int8_t *const *d_in, 
     for (int i = 0; i < batch->nbanks; i++) {
         if (!d_in[i] || !d_accum[i] || nspectra[i] < 0) return VSPEC_ERR_INVALID_ARG;
         if (((uintptr_t)d_in[i] & 15u) || ((uintptr_t)d_accum[i] & 15u)) return VSPEC_ERR_ALIGNMENT;
+    }
+    if (batch->persistent && batch->stall_bank >= 0) {  // one launch with the injected stall, outside the graph
+        const int bank = batch->stall_bank;
+        batch->stall_bank = -1;
+        return vspec_bp_execute(batch->plans.data(), batch->nbanks, d_in, nspectra, d_accum, batch->bp_ctl,
+                                batch->bp_status, bank, (cudaStream_t)stream);
     }
     if (!same_args(batch, d_in, nspectra, d_accum)) {
         vspec_status st = capture_graph(batch, d_in, nspectra, d_accum);
@@ -278,6 +298,62 @@ vspec_status vspec_batch_autotune(vspec_batch *batch, const int8_t *const *d_in,
         cudaGraphExecDestroy(batch->exec);
         batch->exec = nullptr;
     }
+    // the whole batch: per-bank kernels in one graph against one persistent
+    // launch over all banks (where every bank has a ticket body); keep the faster
+    if (result == VSPEC_OK) {
+        auto time_batch = [&](float *ms) -> bool {
+            vspec_status s = vspec_batch_execute(batch, d_in, nspectra, d_accum, stream);
+            cudaEventRecord(t0, st);
+            for (int r = 0; r < reps && s == VSPEC_OK; r++) s = vspec_batch_execute(batch, d_in, nspectra, d_accum, stream);
+            cudaEventRecord(t1, st);
+            return s == VSPEC_OK && cudaEventSynchronize(t1) == cudaSuccess &&
+                   cudaEventElapsedTime(ms, t0, t1) == cudaSuccess;
+        };
+        float ms_graph = 0.f, ms_pers = 0.f;
+        batch->persistent = false;
+        const bool g_ok = time_batch(&ms_graph);
+        // persistent trial: banks whose tuned plan has no ticket body run their
+        // two-kernel plan in it; the tuned plans come back if the graph wins
+        std::vector<vspec_plan *> tuned = batch->plans, alt = batch->plans;
+        bool p_ok = g_ok && batch->nbanks <= 16;
+        for (int i = 0; i < batch->nbanks && p_ok; i++) {
+            if (vspec_bp_supported(tuned[i], nullptr) == VSPEC_OK) continue;
+            const vspec_bank &d = batch->desc[i];
+            alt[i] = nullptr;
+            if (vspec_plan_create_ex(&alt[i], d.nchan, d.ntaps, d.npol, d.mode, d.window, VSPEC_PLAN_TWO_KERNEL) !=
+                    VSPEC_OK ||
+                vspec_bp_supported(alt[i], nullptr) != VSPEC_OK)
+                p_ok = false;
+        }
+        if (p_ok) {
+            batch->plans = alt;
+            p_ok = vspec_batch_set_persistent(batch, 1) == VSPEC_OK && time_batch(&ms_pers) &&
+                   vspec_batch_check(batch) == VSPEC_OK;
+        }
+        cudaStreamSynchronize(st);
+        const bool keep = p_ok && ms_pers < ms_graph;
+        for (int i = 0; i < batch->nbanks; i++) {
+            if (alt[i] == tuned[i]) continue;
+            if (keep) {
+                vspec_plan_destroy(tuned[i]);
+                batch->flags[i] = VSPEC_PLAN_TWO_KERNEL;
+                vspec_plan_get_tuning(alt[i], &batch->tuning[i], nullptr);
+            } else if (alt[i]) {
+                vspec_plan_destroy(alt[i]);
+            }
+        }
+        if (!keep) {
+            batch->plans = tuned;
+            vspec_batch_set_persistent(batch, 0);
+        }
+        cudaStreamSynchronize(st);
+        for (int i = 0; i < batch->nbanks; i++) {
+            const vspec_bank &d = batch->desc[i];
+            const size_t bytes = (size_t)d.nchan * (d.npol == 2 ? 4 : 1) * sizeof(float);
+            if (cudaMemsetAsync(d_accum[i], 0, bytes, st) != cudaSuccess) result = VSPEC_ERR_CUDA;
+        }
+        cudaStreamSynchronize(st);
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     return result;
@@ -293,6 +369,80 @@ vspec_status vspec_batch_bank_tuning(const vspec_batch *batch, int bank, unsigne
 vspec_status vspec_batch_bank_shape(const vspec_batch *batch, int bank, int *col_len, int *tile_cols) {
     if (!batch || bank < 0 || bank >= batch->nbanks) return VSPEC_ERR_INVALID_ARG;
     return vspec_plan_get_shape(batch->plans[bank], col_len, tile_cols);
+}
+
+vspec_status vspec_batch_set_persistent(vspec_batch *batch, int enable) {
+    if (!batch) return VSPEC_ERR_INVALID_ARG;
+    if (batch->exec) {  // the next execute captures the other form
+        cudaGraphExecDestroy(batch->exec);
+        batch->exec = nullptr;
+    }
+    if (!enable) {
+        batch->persistent = false;
+        return VSPEC_OK;
+    }
+    if (batch->nbanks > 16) {
+        vspec_set_last_error("the persistent launch holds at most 16 banks");
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    // a bank whose plan has no ticket body in the kernel gets its two-kernel plan
+    for (int i = 0; i < batch->nbanks; i++) {
+        const char *why = nullptr;
+        if (vspec_bp_supported(batch->plans[i], &why) == VSPEC_OK) continue;
+        const vspec_bank &d = batch->desc[i];
+        vspec_plan *p = nullptr;
+        vspec_status st = vspec_plan_create_ex(&p, d.nchan, d.ntaps, d.npol, d.mode, d.window, VSPEC_PLAN_TWO_KERNEL);
+        if (st != VSPEC_OK) return st;
+        if (vspec_bp_supported(p, &why) != VSPEC_OK) {
+            vspec_plan_destroy(p);
+            vspec_set_last_error(why);
+            return VSPEC_ERR_UNSUPPORTED;
+        }
+        vspec_plan_destroy(batch->plans[i]);
+        batch->plans[i] = p;
+        batch->flags[i] = VSPEC_PLAN_TWO_KERNEL;
+        vspec_plan_get_tuning(p, &batch->tuning[i], nullptr);
+    }
+    if (!batch->bp_ctl) {
+        if (cudaMalloc(&batch->bp_ctl, sizeof(int) * (2 + 2 * 16)) != cudaSuccess ||
+            cudaMalloc(&batch->bp_status, sizeof(int)) != cudaSuccess ||
+            cudaMemset(batch->bp_status, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(batch->bp_ctl);
+            cudaFree(batch->bp_status);
+            batch->bp_ctl = batch->bp_status = nullptr;
+            return VSPEC_ERR_OOM;
+        }
+    }
+    batch->persistent = true;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_batch_get_persistent(const vspec_batch *batch, int *enabled) {
+    if (!batch || !enabled) return VSPEC_ERR_INVALID_ARG;
+    *enabled = batch->persistent ? 1 : 0;
+    return VSPEC_OK;
+}
+
+vspec_status vspec_batch_check(vspec_batch *batch) {
+    if (!batch) return VSPEC_ERR_INVALID_ARG;
+    if (!batch->bp_status) return VSPEC_OK;
+    int h = 0;
+    if (cudaMemcpy(&h, batch->bp_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return VSPEC_ERR_CUDA;
+    if (!h) return VSPEC_OK;
+    if (cudaMemset(batch->bp_status, 0, sizeof(int)) != cudaSuccess) return VSPEC_ERR_CUDA;
+    vspec_set_last_error("a bounded wait of the persistent multi-bank kernel gave up; results are incomplete");
+    return VSPEC_ERR_DEVICE_TIMEOUT;
+}
+
+vspec_status vspec_batch_inject_stall(vspec_batch *batch, int bank) {
+    if (!batch || bank < 0 || bank >= batch->nbanks) return VSPEC_ERR_INVALID_ARG;
+    if (!batch->persistent) {
+        vspec_set_last_error("only the persistent form waits on other CTAs' work");
+        return VSPEC_ERR_UNSUPPORTED;
+    }
+    batch->stall_bank = bank;
+    return VSPEC_OK;
 }
 
 vspec_status vspec_batch_bank_flags(const vspec_batch *batch, int bank, unsigned *flags) {

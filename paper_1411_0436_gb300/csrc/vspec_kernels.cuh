@@ -667,18 +667,24 @@ struct ColDir {
     static_assert(N2 >= 2 && N2 <= 256 && C >= 8, "column shapes of this kernel");
 };
 
+// Tile x of the direct-mode register-column kernel A over spectra s_beg ..
+// s_end - 1 of a chunk: spectrum s of the chunk is absolute spectrum s0 + s
+// and goes to Zc[s] (the chunk holds sc spectra). All 512 threads of the CTA
+// take part; the function ends with a barrier. load_twc: load the first-pass
+// twiddles (they stay in shared memory for later tiles of the same launch).
 template <int N2>
-__global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__ ColParams p) {
+__device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long long s0, int sc, int x, int s_beg,
+                                            int s_end, unsigned char *smem_raw, bool load_twc) {
     using G = ColDir<N2>;
     constexpr int PTS = G::PTS, C = G::C, SPB = G::SPB, R1 = G::R1, R2 = G::R2, M1 = G::M1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *raw = reinterpret_cast<uint32_t *>(smem_raw);                        // [2][SPB][PTS]
     P2 *data = reinterpret_cast<P2 *>(raw + 2 * SPB * PTS);                        // [SPB][PTS]
     float2 *tws = reinterpret_cast<float2 *>(data + (G::kOnePass ? 0 : SPB * PTS));  // [N2][C]
     float2 *twc = tws + PTS;                                                       // [M1][R1-1]
     float *wins = reinterpret_cast<float *>(twc + G::TWC);                         // [N2][C]
     const int t = threadIdx.x;
-    for (int e = t; e < G::TWC; e += blockDim.x) twc[e] = __ldg(p.twA + p.pass[0].off + e);
+    if (load_twc)
+        for (int e = t; e < G::TWC; e += 512) twc[e] = __ldg(p.twA + p.pass[0].off + e);
     // sample (pos e of the tile) of spectrum row rb, times the window value when there is one
     auto sample = [&](const uint32_t *rb, int e) {
         P2 v = unpack_p2(rb[e] ^ 0x80808080u);
@@ -688,15 +694,9 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
         }
         return v;
     };
-    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
-    for (long long f = sp.lo; f < sp.hi;) {
-        const long long base = f / p.sc * p.sc;  // first item of this super-tile
-        const int x = (int)(f / p.sc) * sp.G + sp.r;
-        const int s_beg = (int)(f - base);
-        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
-        f = base + s_end;
+    {
         const int n1_0 = x * C;
-        for (int e = t; e < PTS; e += blockDim.x) {  // W_N^(n1 k2(pos)); window values h[n1 + N1 n2]
+        for (int e = t; e < PTS; e += 512) {  // W_N^(n1 k2(pos)); window values h[n1 + N1 n2]
             tws[e] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
             if (p.win) wins[e] = __ldg(p.coef + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
         }
@@ -704,10 +704,10 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
         auto stage = [&](int sb, int buf) {
             const int nbb = min(SPB, s_end - sb);
             constexpr int per_row = C / 4, per_frame = PTS / 4;
-            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
+            for (int e = t; e < nbb * per_frame; e += 512) {
                 const int u = e / per_frame, r = e % per_frame;
                 const int n2 = r / per_row, ch = r % per_row;
-                const long long fr = p.s0 + sb + u;
+                const long long fr = s0 + sb + u;
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
                                       (long long)p.N1 * n2 + ch * 4;
                 uint32_t *dst = raw + (buf * SPB + u) * PTS + n2 * C + ch * 4;
@@ -734,8 +734,8 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
 #pragma unroll
                         for (int q = 0; q < N2; q++) v[q] = sample(rb + sb * PTS, q * C + c);
                         Dft<N2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N + n1_0 + c;
-                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
                         for (int q = 1; q < N2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[q * C + c]);
@@ -771,9 +771,9 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
 #pragma unroll
                         for (int q = 0; q < R2; q++) v[q] = d[q * C];
                         Dft<R2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(p.Z) + (size_t)(s_base + sb) * p.N +
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
-                        if (!dbg_ok(s_base + sb < p.sc && n1_0 + c < p.N1, kDbgScratch)) continue;
+                        if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
                         for (int q = 0; q < R2; q++) z[(size_t)q * p.N1] = cmul(v[q], tws[(b * R2 + q) * C + c]);
                     }
@@ -781,6 +781,22 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
             }
         }
         __syncthreads();  // the column passes are done with the twiddle tile and data
+    }
+}
+
+template <int N2>
+__global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__ ColParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
+    bool first = true;
+    for (long long f = sp.lo; f < sp.hi;) {
+        const long long base = f / p.sc * p.sc;  // first item of this super-tile
+        const int x = (int)(f / p.sc) * sp.G + sp.r;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+        coldir_tile<N2>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first);
+        first = false;
     }
 }
 

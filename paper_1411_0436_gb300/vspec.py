@@ -115,6 +115,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vspec_batch_bank_tuning.restype = i
         lib.vspec_batch_bank_shape.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         lib.vspec_batch_bank_shape.restype = i
+        lib.vspec_batch_set_persistent.argtypes = [vp, i]
+        lib.vspec_batch_set_persistent.restype = i
+        lib.vspec_batch_get_persistent.argtypes = [vp, ctypes.POINTER(i)]
+        lib.vspec_batch_get_persistent.restype = i
+        lib.vspec_batch_check.argtypes = [vp]
+        lib.vspec_batch_check.restype = i
+        lib.vspec_batch_inject_stall.argtypes = [vp, i]
+        lib.vspec_batch_inject_stall.restype = i
         lib.vspec_plan_create_shaped.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, ctypes.c_uint, i, i]
         lib.vspec_plan_create_shaped.restype = i
         lib.vspec_plan_get_shape.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -561,6 +569,32 @@ class Batch:
         if st != OK:
             raise VspecError(st, "vspec_batch_bank_shape")
         return int(a.value), int(b.value)
+
+    def set_persistent(self, enable: bool = True) -> None:
+        """One persistent launch over every bank (vspec_batch_set_persistent), or per-bank kernels."""
+        st = load().vspec_batch_set_persistent(self.handle, 1 if enable else 0)
+        if st != OK:
+            raise VspecError(st, "vspec_batch_set_persistent")
+
+    @property
+    def persistent(self) -> bool:
+        v = ctypes.c_int()
+        st = load().vspec_batch_get_persistent(self.handle, ctypes.byref(v))
+        if st != OK:
+            raise VspecError(st, "vspec_batch_get_persistent")
+        return bool(v.value)
+
+    def check(self) -> None:
+        """Raise if a bounded wait of the persistent kernel gave up (vspec_batch_check)."""
+        st = load().vspec_batch_check(self.handle)
+        if st != OK:
+            raise VspecError(st, "vspec_batch_check")
+
+    def inject_stall(self, bank: int) -> None:
+        """Make the next persistent execute's row tickets of `bank` wait for nothing (failure tests)."""
+        st = load().vspec_batch_inject_stall(self.handle, bank)
+        if st != OK:
+            raise VspecError(st, "vspec_batch_inject_stall")
 
     def bank_tuning(self, i: int):
         """(flags, launch shape as a dict) of the plan bank i runs."""
