@@ -537,7 +537,7 @@ VSPEC_API vspec_status vspec_batch_bank_shape(const vspec_batch *batch, int bank
  * 512-thread CTA per SM) instead of every bank's kernels. That kernel runs
  * all banks' work as tickets in three phases, handed out in order by an
  * atomic counter: kernel-A tiles of every bank (the register-column forms,
- * into the bank's chunk scratch), then row tickets (16 spectra of one
+ * into the bank's chunk scratch), then row tickets (32 spectra of one
  * 2048-point row, or of a one-row transform with its pre-filter), then fold
  * tickets (512 channels: the row tickets' sums, added in order and
  * compensated, into the caller's accumulator). A bank's row tickets wait

@@ -13,7 +13,7 @@
 //      256-thread groups take half the spectra each, sum their detected
 //      spectra, and store the sum into set u of the bank's partial sums (one
 //      writer per set entry);
-//   F: fold tickets of every bank (512 channels): the sets added in order
+//   F: fold tickets of every bank (2048 channels): the sets added in order
 //      (compensated) into the caller's accumulator in channel order.
 // A bank's B tickets wait (bounded, thread 0) until all its A tickets are
 // done, its F tickets until all its B tickets are done. Every wait points to
@@ -269,20 +269,21 @@ __device__ __forceinline__ void bp_ticket_rowfir(const BpBank &bk, int u, unsign
     }
 }
 
-// Fold ticket i of a bank: channels 512 i .. 512 i + 511, every set in order
-// (compensated), added into the caller's accumulator.
+// Fold ticket i of a bank: channels kBpFoldChannels i .. + kBpFoldChannels -
+// 1, every set in order (compensated), added into the caller's accumulator.
+constexpr int kBpFoldChannels = 2048;
 __device__ __forceinline__ void bp_ticket_fold(const BpBank &bk, int i) {
     const int N = bk.b.N, N1 = bk.b.N1, N2 = bk.N2;
-    const int k = i * 512 + threadIdx.x;
-    if (k >= N) return;
-    const int k1 = k / N2, k2 = k - k1 * N2;
-    const size_t pos = (size_t)__ldg(bk.invA + k2) * N1 + __ldg(bk.invB + k1);
     const int nsets = (bk.nspectra + bk.TB - 1) / bk.TB;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f), c = s;
-    for (int u = 0; u < nsets; u++) kahan_add(s, c, __ldcg(bk.sets + (size_t)u * N + pos));
-    kahan_settle(s, c);
-    const float4 o = bk.acc[k];
-    bk.acc[k] = make_float4(o.x + s.x, o.y + s.y, o.z + s.z, o.w + s.w);
+    for (int k = i * kBpFoldChannels + threadIdx.x; k < min(N, (i + 1) * kBpFoldChannels); k += 512) {
+        const int k1 = k / N2, k2 = k - k1 * N2;
+        const size_t pos = (size_t)__ldg(bk.invA + k2) * N1 + __ldg(bk.invB + k1);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f), c = s;
+        for (int u = 0; u < nsets; u++) kahan_add(s, c, __ldcg(bk.sets + (size_t)u * N + pos));
+        kahan_settle(s, c);
+        const float4 o = bk.acc[k];
+        bk.acc[k] = make_float4(o.x + s.x, o.y + s.y, o.z + s.z, o.w + s.w);
+    }
 }
 
 #ifdef VSPEC_DEFINE_BP_KERNEL  // defined in one translation unit (vspec_bp.cu)
@@ -290,8 +291,26 @@ __global__ void __launch_bounds__(512, 1) bp_kernel(const __grid_constant__ BpPa
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_t, s_ok;
     const int total = q.offA[q.nbanks] + q.offB[q.nbanks] + q.offF[q.nbanks];
+    // Thread 0 holds the next ticket, fetched while the current one runs,
+    // and whether its producers were already done when it looked (counters
+    // only grow, so a yes stays true). A CTA's prefetched ticket is later
+    // than its current one, so the earliest unfinished ticket is always some
+    // CTA's current ticket and can run.
+    int next = 0;
+    bool next_ready = false;
+    auto producers = [&](const BpTicket &k, const int **ctr, int *target) {
+        const BpBank &bk = q.banks[k.bank];
+        *ctr = k.phase == 1 ? q.ctl + 2 + 2 * k.bank : q.ctl + 3 + 2 * k.bank;
+        *target = k.phase == 1 ? bk.nA : bk.nB;
+        return k.phase == 1 || k.phase == 2;
+    };
+    if (threadIdx.x == 0) next = atomicAdd(q.ctl, 1);
     for (;;) {
-        if (threadIdx.x == 0) s_t = atomicAdd(q.ctl, 1);
+        if (threadIdx.x == 0) {
+            s_t = next;
+            s_ok = next_ready;
+            next = atomicAdd(q.ctl, 1);
+        }
         __syncthreads();
         const int t = s_t;
         if (t >= total) break;
@@ -300,9 +319,16 @@ __global__ void __launch_bounds__(512, 1) bp_kernel(const __grid_constant__ BpPa
         int *doneA = q.ctl + 2 + 2 * k.bank, *doneB = doneA + 1;
         if (threadIdx.x == 0) {
             bool ok = k.phase >= 0;
-            if (k.phase == 1) ok = bp_wait(q, doneA, bk.nA);
-            else if (k.phase == 2) ok = bp_wait(q, doneB, bk.nB);
+            const int *ctr;
+            int target;
+            if (ok && !s_ok && producers(k, &ctr, &target)) ok = bp_wait(q, ctr, target);
             s_ok = ok;
+            // look at the next ticket's producers now; the answer is used next time
+            next_ready = false;
+            if (next < total) {
+                const BpTicket kn = bp_decode(q, next);
+                next_ready = !producers(kn, &ctr, &target) || ld_acquire_gpu(ctr) >= target;
+            }
         }
         __syncthreads();
         if (!s_ok) continue;  // aborted: skip what is left
@@ -315,7 +341,7 @@ __global__ void __launch_bounds__(512, 1) bp_kernel(const __grid_constant__ BpPa
             bp_ticket_fold(bk, k.i);
         }
         __syncthreads();  // the ticket's stores are issued; shared memory is free
-        if (threadIdx.x == 0 && k.phase < 2) {
+        if (threadIdx.x == 32 && k.phase < 2) {  // warp 1 signals while warp 0 takes the next ticket
             __threadfence();
             atomicAdd(k.phase == 0 ? doneA : doneB, 1);
         }
