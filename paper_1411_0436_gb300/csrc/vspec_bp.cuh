@@ -306,9 +306,10 @@ __global__ void __launch_bounds__(512, 1) bp_kernel(const __grid_constant__ BpPa
     };
     if (threadIdx.x == 0) next = atomicAdd(q.ctl, 1);
     for (;;) {
+        bool cur_ready = false;  // thread 0 only (shared s_ok is written only between the two barriers)
         if (threadIdx.x == 0) {
             s_t = next;
-            s_ok = next_ready;
+            cur_ready = next_ready;
             next = atomicAdd(q.ctl, 1);
         }
         __syncthreads();
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(512, 1) bp_kernel(const __grid_constant__ BpPa
             bool ok = k.phase >= 0;
             const int *ctr;
             int target;
-            if (ok && !s_ok && producers(k, &ctr, &target)) ok = bp_wait(q, ctr, target);
+            if (ok && !cur_ready && producers(k, &ctr, &target)) ok = bp_wait(q, ctr, target);
             s_ok = ok;
             // look at the next ticket's producers now; the answer is used next time
             next_ready = false;

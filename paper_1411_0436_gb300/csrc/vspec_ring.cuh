@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(512, 1) ring_kernel(const __grid_constant__ Ri
     int *doneA = q.ctl + 2, *doneB = q.ctl + 2 + q.nslot;
     const size_t slot_elems = (size_t)q.S * q.b.N;
     bool twc_loaded = false;
+    // (tickets are fetched when the CTA is free: a ticket fetched ahead would
+    // wait behind the current one and hold back the slot it frees)
     for (;;) {
         if (threadIdx.x == 0) s_t = atomicAdd(q.ctl, 1);
         __syncthreads();
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(512, 1) ring_kernel(const __grid_constant__ Ri
             }
         }
         __syncthreads();  // the ticket's stores are issued; shared memory is free
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 32) {  // warp 1 signals while warp 0 takes the next ticket
             __threadfence();
             atomicAdd((k.kind == 0 ? doneA : doneB) + k.c, 1);
         }
