@@ -297,9 +297,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         bank = dataclasses.replace(bank, nspectra=min(args.spectra, bank.nspectra))
     # each rank is an independent beam: its own seeded input
     x = workloads.generate(bank, beam_seed(rank, config))
+    nsub = max(1, args.nsub)
+    if nsub > 1:  # sub-band input [time][sub][pol][re, im]: independent seeded bands
+        x = np.ascontiguousarray(np.stack([x] + [workloads.generate(bank, beam_seed(rank, config) + 31 * b)
+                                                 for b in range(1, nsub)], axis=1))
+        args.no_variants = args.no_cpu_baseline = args.no_e2e = True
     in_bytes = x.nbytes
     n, S = bank.nchan, bank.nspectra
-    plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window, args.plan_flags)
+    plan = Plan(n, bank.ntaps, bank.npol, bank.mode, bank.window, args.plan_flags, nsub=nsub)
     plan_desc = plan.describe()  # decomposition and kernel forms, for the JSON line
     d_in = torch.from_numpy(x.view(np.uint8).reshape(-1)).to(dev)
     acc = torch.zeros(plan.out_floats, dtype=torch.float32, device=dev)
@@ -358,16 +363,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clk = clocks.stop()
 
     total_ms = reduce_max(total_ms, dist, dev)
-    value = whole_job_ghz(world, args.steps, S, n, total_ms)
+    value = whole_job_ghz(world, args.steps, S, n * nsub, total_ms)
 
     # dominant kernel: live CUDA-event times
     peak, peak_kind = _peaks()
-    per_spec_bytes = n * bank.npol * 2 + 2.0 * n * 16 / S  # int8 input once + accumulator RMW per dump
+    per_spec_bytes = (n * bank.npol * 2 + 2.0 * n * 16 / S) * nsub  # int8 input once + accumulator RMW per dump
     dom = max(stats, key=lambda r: r[3])
     name, launches, spectra, kms = dom
-    achieved = (spectra * per_spec_bytes) / (kms * 1e-3) / 1e9
+    # (a sub-band call's launches each count the spectra of one band)
+    achieved = (spectra * per_spec_bytes / nsub) / (kms * 1e-3) / 1e9
     spl = spectra / max(1, launches)
-    traffic = _traffic(config, name, spl)
+    traffic = _traffic(config, name, spl) if nsub == 1 else None
     path_bytes = args.steps * S * per_spec_bytes
     kernels = {r[0]: {"launches": r[1], "total_ms": round(r[3], 4),
                       "share": round(r[3] / max(1e-9, sum(q[3] for q in stats)), 4)} for r in stats}
@@ -376,10 +382,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # 4P FIR + 5 log2 N FFT + detection/accumulation) against the CUDA-core peak
     taps_eff = bank.ntaps if bank.mode == workloads.PFB else 1
     flop_per_sample = 4 * taps_eff + 5 * int(np.log2(n)) + (8 if bank.npol == 2 else 4)
-    flop_per_spec = flop_per_sample * n * bank.npol
+    flop_per_spec = flop_per_sample * n * bank.npol * nsub
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = nsm * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    alu_achieved = spectra * flop_per_spec / (kms * 1e-3) / 1e12
+    alu_achieved = spectra * flop_per_spec / nsub / (kms * 1e-3) / 1e12
 
     # end to end through vspec_execute_host: pinned host input, chunked copies
     # overlapped with the compute on plan-owned streams, result read back to
@@ -537,7 +543,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[config], "name": config, "nchan": n, "ntaps": bank.ntaps,
-                       "npol": bank.npol, "nspectra": S, "input_bytes": int(in_bytes),
+                       "npol": bank.npol, "nspectra": S, "nsub": nsub, "input_bytes": int(in_bytes),
                        "l2": "flushed between steps (256 MiB write outside the timed interval)",
                        "parallelism": f"replicas x{world} (independent beams)"},
             "ms_per_step_median": median_ms,
@@ -728,6 +734,9 @@ def main():
                     help="bandwidth against FFT length and accumulation length (Fig. 3 shape)")
     ap.add_argument("--plan-flags", type=int, default=0,
                     help="VSPEC_PLAN_* flags of the timed plan (profiling other plan forms; 0: the default)")
+    ap.add_argument("--nsub", type=int, default=1,
+                    help="sub-band mode: NSUB bands of the workload interleaved per sample (vspec_plan_create_sb); "
+                         "the rate counts every band; no variants, CPU baseline or end-to-end run")
     ap.add_argument("--spectra", type=int, default=0,
                     help="channelize only the first SPECTRA spectra of the dump (smaller profiling captures)")
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default=CONFIG_NAME,

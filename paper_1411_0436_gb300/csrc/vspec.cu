@@ -523,6 +523,9 @@ constexpr int kMaxWaves = 4;    // largest tuned launch, in waves of CTAs
 constexpr size_t kRingSlotBytes = 32u << 20;
 constexpr size_t kRingSetBytes = 16u << 20;
 constexpr int kRingSlotsPerLaunch = 4096;
+// Sub-band input read in place: chunks of about this much input (all bands),
+// so that the bands after the first find it in L2.
+constexpr size_t kSbInPlaceBytes = 32u << 20;
 
 // Partial-sum slots a kernel-B launch of n CTAs uses: a CTA's rank among the
 // CTAs that share a row tile stays below n / tiles + 2 (span_slot).
@@ -1115,6 +1118,9 @@ vspec_status vspec_plan_create_shaped(vspec_plan **out, int nchan, int ntaps, in
     return VSPEC_OK;
 }
 
+static bool sb_in_place(const vspec_plan *p, int nsub);
+static vspec_plan *sb_plan(vspec_plan *p);
+
 vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int npol, int nsub,
                                   vspec_mode mode, vspec_window window, unsigned flags) {
     if (!out) return VSPEC_ERR_INVALID_ARG;
@@ -1128,6 +1134,7 @@ vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int np
     if (st != VSPEC_OK || nsub == 1) return st;
     vspec_plan *p = *out;
     p->nsub = nsub;
+    if (sb_in_place(sb_plan(p), nsub)) return VSPEC_OK;  // kernel A reads each band in place: no de-interleave scratch
     const int Peff = mode == VSPEC_PFB ? ntaps : 1;
     const size_t per_spec = (size_t)nchan * npol * 2;  // bytes of one sub-band per spectrum
     p->sb_chunk = (int)std::max<size_t>(1, (64u << 20) / (per_spec * nsub));
@@ -1341,6 +1348,96 @@ vspec_status vspec_plan_trim_scratch(vspec_plan *plan) {
 
 static vspec_status execute_one(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
                                 cudaStream_t st);
+static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
+                                   cudaStream_t st, cudaEvent_t before_fold, int band = -1, int nsub = 1);
+
+// The plan a sub-band call of p runs: a fused plan's own two-kernel plan
+// (which its long calls run anyway), else p.
+static vspec_plan *sb_plan(vspec_plan *p) { return p->fused && p->assist ? p->assist : p; }
+
+// Whether kernel A of plan p can read a band of nsub-band interleaved input
+// in place: the dual-pol register-column forms on the plain two-kernel path.
+static bool sb_in_place(const vspec_plan *p, int nsub) {
+    return nsub > 1 && p->npol == 2 && !p->fused && !p->ring && !p->tc && !p->tc_cols && !p->fir_b && !p->kahan &&
+           (std::strcmp(p->formA, "colreg") == 0 || std::strcmp(p->formA, "coldir") == 0);
+}
+
+static void make_params(const vspec_plan *p, const int8_t *d_in, int nspectra, vspec::ColParams &ca,
+                        vspec::RowParams &cb);
+
+// Whether every band of a sub-band call fits one kernel-A and one kernel-B
+// launch per chunk (run_bands): the tiled fold, the slots of nsub bands
+// within the plan's partial sums, at least one spectrum of every band in the
+// chunk scratch.
+static bool bands_fit(const vspec_plan *p, int nsub) {
+    if (!sb_in_place(p, nsub) || !p->fold2048 || p->sc_alloc < nsub) return false;
+    const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
+    const int tilesB = nsub * (p->N2 / p->RB);
+    return (nB / tilesB + 2) * nsub <= p->slots_cap;
+}
+
+// Every band of a sub-band call in one kernel-A and one kernel-B launch per
+// chunk. Kernel A's tile X is column tile X / nsub of band X mod nsub, so
+// adjacent tiles (whose CTAs run together) read the same input lines and the
+// input comes from HBM once. A spectrum's intermediate holds the bands one
+// after another, a virtual spectrum of nsub N points whose nsub N2 rows kernel
+// B transforms as usual; the partial sums are slots of that virtual spectrum,
+// and one fold per band reads its part.
+static vspec_status run_bands(vspec_plan *p, int nsub, const int8_t *d_in, int nspectra, float *d_accum,
+                              cudaStream_t st) {
+    const int nA = p->blocks_a > 0 ? p->blocks_a : p->num_sms * p->occA;
+    const int nB = p->blocks_b > 0 ? p->blocks_b : p->num_sms * p->occB;
+    const int cap = std::max(1, std::min(p->sc_max, p->sc_alloc / nsub));  // spectra of all bands in the scratch
+    const int nchunks = (nspectra + cap - 1) / cap;
+    const int sc_full = (nspectra + nchunks - 1) / nchunks;
+    const int tilesB = nsub * (p->N2 / p->RB);
+    const long long NV = (long long)nsub * p->N;
+    const int slots = (int)(std::min<long long>(nB, (long long)tilesB * sc_full) / tilesB + 2);
+    VSPEC_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)slots * NV * sizeof(float4), st));
+    vspec::ColParams ca;
+    vspec::RowParams cb;
+    make_params(p, d_in, nspectra, ca, cb);
+    ca.nsub = nsub;
+    ca.band = -1;
+    ca.zstride = NV;
+    ca.tiles = nsub * (p->N1 / p->C);
+    cb.N = (int)NV;
+    cb.tiles = tilesB;
+    cb.slots = slots;
+    cb.store = 0;
+    for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
+        const int sc = std::min(sc_full, nspectra - s0);
+        ca.s0 = s0;
+        ca.sc = sc;
+        void *argsA[] = {&ca};
+        int ga = (int)std::min<long long>(nA, (long long)ca.tiles * sc);
+        ga = std::max(ca.G, ga / ca.G * ca.G);
+        vspec_status r = launch(p, 0, sc * nsub, p->kernelA, dim3(ga), dim3(p->TA), argsA, p->smemA, st);
+        if (r != VSPEC_OK) return r;
+        cb.s0 = s0;
+        cb.sc = sc;
+        vspec::TcStatus ts{p->tc_status, g_wait_limit.load()};
+        void *argsB[] = {&cb, &ts};
+        const int gb = (int)std::min<long long>(nB, (long long)tilesB * sc);
+        r = launch(p, 1, sc * nsub, p->kernelB, dim3(gb), dim3(p->TB), argsB, p->smemB, st);
+        if (r != VSPEC_OK) return r;
+    }
+    // one tiled fold per band: its positions are [b N, (b + 1) N) of every slot
+    using namespace vspec;
+    const int N2 = p->N2, Nv = (int)NV, groups = slots, stride = 1;
+    const bool wide = N2 >= 64;
+    const void *k = wide ? (const void *)reduce2048_kernel<2, 32, 1> : (const void *)reduce2048_kernel<2, 8, 4>;
+    const int *ia = p->invA;
+    for (int b = 0; b < nsub; b++) {
+        const void *part = reinterpret_cast<const float4 *>(p->partial) + (size_t)b * p->N;
+        void *outp = d_accum + (size_t)b * p->N * 4;
+        void *argsT[] = {&part, (void *)&groups, (void *)&stride, (void *)&Nv, (void *)&N2, &ia, &outp};
+        vspec_status r = launch(p, 2, nspectra, k, dim3(N2 / 16 * 16 * (wide ? 4 : 16)), dim3(wide ? 256 : 512),
+                                argsT, 0, st);
+        if (r != VSPEC_OK) return r;
+    }
+    return VSPEC_OK;
+}
 
 vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, float *d_accum,
                            void *stream) {
@@ -1350,11 +1447,29 @@ vspec_status vspec_execute(vspec_plan *plan, const int8_t *d_in, int nspectra, f
     cudaStream_t st = (cudaStream_t)stream;
     vspec_plan *p = plan;
     if (p->nsub == 1) return execute_one(p, d_in, nspectra, d_accum, st);
-    // sub-band modes: de-interleave a chunk of spectra, then every sub-band
     const int Peff = p->mode == VSPEC_PFB ? p->P : 1;
     const size_t wbytes = (size_t)p->npol * 2;             // one sample of every polarisation
-    const long long slot = (long long)(p->sb_chunk + Peff - 1) * p->N;  // samples per slot
     const size_t outw = (size_t)p->N * (p->npol == 2 ? 4 : 1);
+    vspec_plan *t = sb_plan(p);
+    if (bands_fit(t, p->nsub)) return run_bands(t, p->nsub, d_in, nspectra, d_accum, st);
+    if (sb_in_place(t, p->nsub)) {
+        // the register-column kernel A reads each band of the [time][sub][pol]
+        // input in place; the bands of a chunk run back to back, so the chunk
+        // (about kSbInPlaceBytes of input) comes from HBM once and from L2 after
+        const size_t per_spec = (size_t)p->N * p->nsub * wbytes;
+        const int chunk = (int)std::max<size_t>(16, kSbInPlaceBytes / per_spec);
+        for (int s0 = 0; s0 < nspectra; s0 += chunk) {
+            const int cnt = std::min(chunk, nspectra - s0);
+            for (int b = 0; b < p->nsub; b++) {
+                vspec_status r = run_two_kernel(t, d_in + (size_t)s0 * per_spec, cnt, d_accum + (size_t)b * outw, st,
+                                                nullptr, b, p->nsub);
+                if (r != VSPEC_OK) return r;
+            }
+        }
+        return VSPEC_OK;
+    }
+    // other sub-band plans: de-interleave a chunk of spectra, then every sub-band
+    const long long slot = (long long)(p->sb_chunk + Peff - 1) * p->N;  // samples per slot
     for (int s0 = 0; s0 < nspectra; s0 += p->sb_chunk) {
         const int cnt = std::min(p->sb_chunk, nspectra - s0);
         const long long M = (long long)(cnt + Peff - 1) * p->N;
@@ -1475,7 +1590,7 @@ static void make_params(const vspec_plan *p, const int8_t *d_in, int nspectra, v
 }
 
 static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspectra, float *d_accum,
-                                   cudaStream_t st, cudaEvent_t before_fold) {
+                                   cudaStream_t st, cudaEvent_t before_fold, int band, int nsub) {
     const size_t accel = p->npol == 2 ? sizeof(float4) : sizeof(float);
     // one full wave of CTAs per launch unless tuned; the work is split evenly
     // over them (block_span), so every SM stays busy to the end of a launch
@@ -1499,6 +1614,10 @@ static vspec_status run_two_kernel(vspec_plan *p, const int8_t *d_in, int nspect
     make_params(p, d_in, nspectra, ca, cb);
     cb.slots = slots;
     cb.store = store;
+    if (band >= 0) {  // kernel A reads band `band` of the nsub-band [time][sub][pol] input in place
+        ca.nsub = nsub;
+        ca.band = band;
+    }
 
     for (int s0 = 0; s0 < nspectra; s0 += sc_full) {
         const int sc = std::min(sc_full, nspectra - s0);

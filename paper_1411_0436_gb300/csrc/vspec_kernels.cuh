@@ -84,6 +84,12 @@ struct ColParams {
     unsigned wait_limit;         // polls of that wait
     int bterms;                  // fp16 parts of the fused tensor-core operand: 1 (hi) or 2 (hi, lo)
     long long nframes;           // frames the call's input holds (bounds checks of debug builds)
+    // sub-band input read in place (register-column kernels): sample m of band
+    // b is word m nsub + b of the input, [time][sub][pol]; nsub = 1: plain.
+    // band = -1: every band in one launch, tile X being tile X / nsub of band
+    // X mod nsub, band b's spectra at Z + b N with a spectrum stride of zstride
+    int nsub = 1, band = 0;
+    long long zstride = 0;  // scratch elements per spectrum (0: N)
 };
 
 struct RowParams {
@@ -488,7 +494,7 @@ struct ColReg {
 // stay in shared memory for later tiles of the same launch).
 template <int N2, int R1>
 __device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long long s0, int sc, int x, int s_beg,
-                                            int s_end, unsigned char *smem_raw, bool load_twc) {
+                                            int s_end, unsigned char *smem_raw, bool load_twc, int band = 0) {
     using G = ColReg<N2, R1>;
     constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
     constexpr int SS = G::SS;
@@ -499,6 +505,7 @@ __device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long l
     float2 *twc = reinterpret_cast<float2 *>(cfs + PT * PTS);          // [N2/R1][R1-1]
     const int t = threadIdx.x;                                         // point n2 * C + c
     const int D = PT - p.P;                                            // leading zero taps
+    const size_t zs = p.zstride > 0 ? (size_t)p.zstride : (size_t)p.N;  // scratch spectrum stride
     // first-pass twiddles W_N2^(j q) (ordered before use by the loop's barriers)
     if (load_twc)
         for (int e = t; e < G::TWC; e += PTS) twc[e] = __ldg(p.twA + p.pass[0].off + e);
@@ -520,11 +527,27 @@ __device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long l
         for (int k = 0; k < PT - 1; k++) {
             long long fr = sabs - D + k;
             if (fr < 0) fr = 0;
-            win[k] = unpack_p2((dbg_ok(fr < p.nframes, kDbgInput) ? load_raw<2>(p.in, fr * p.N + n_pt) : 0u) ^ 0x80808080u);
+            win[k] = unpack_p2((dbg_ok(fr < p.nframes, kDbgInput) ? load_raw<2>(p.in, (fr * p.N + n_pt) * p.nsub + band)
+                                                                   : 0u) ^ 0x80808080u);
         }
         // the newest frames of SPB spectra, one batch ahead, 16-byte copies
+        // (sub-band input: 4-byte copies of this band's samples, nsub words apart)
         auto stage = [&](int sb, int buf) {
             const int nbb = min(SPB, s_end - sb);
+            if (p.nsub > 1) {
+                for (int e = t; e < nbb * PTS; e += PTS) {
+                    const int u = e / PTS, r = e % PTS;  // r = n2 C + c
+                    const long long fr = s0 + sb + u + p.P - 1;
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) +
+                                          (fr * p.N + n1_0 + (long long)p.N1 * (r / C) + r % C) * p.nsub + band;
+                    uint32_t *dst = raw + (buf * SPB + u) * PTS + r;
+                    if (dbg_ok(fr < p.nframes, kDbgInput))
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                                     :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                return;
+            }
             constexpr int per_row = C / 4, per_frame = PTS / 4;
             for (int e = t; e < nbb * per_frame; e += PTS) {
                 const int u = e / per_frame, r = e % per_frame;
@@ -575,7 +598,7 @@ __device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long l
 #pragma unroll
                         for (int q = 0; q < N2; q++) v[q] = data[sb * SS + q * C + c];
                         Dft<N2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * zs + n1_0 + c;
                         if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
@@ -613,7 +636,7 @@ __device__ __forceinline__ void colreg_tile(const ColParams &p, void *Zc, long l
 #pragma unroll
                         for (int q = 0; q < R2; q++) v[q] = d[q * C];
                         Dft<R2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N +
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * zs +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
                         if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
@@ -637,7 +660,13 @@ __global__ void __launch_bounds__(512, 1) fir_colreg_kernel(const __grid_constan
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
-        colreg_tile<N2, R1>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first);
+        if (p.band < 0) {  // every band in this launch: adjacent tiles are the bands of one column tile
+            const int band = x % p.nsub;
+            colreg_tile<N2, R1>(p, reinterpret_cast<P2 *>(p.Z) + (size_t)band * p.N, p.s0, p.sc, x / p.nsub, s_beg,
+                                s_end, smem_raw, first, band);
+        } else {
+            colreg_tile<N2, R1>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first, p.band);
+        }
         first = false;
     }
 }
@@ -674,7 +703,7 @@ struct ColDir {
 // twiddles (they stay in shared memory for later tiles of the same launch).
 template <int N2>
 __device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long long s0, int sc, int x, int s_beg,
-                                            int s_end, unsigned char *smem_raw, bool load_twc) {
+                                            int s_end, unsigned char *smem_raw, bool load_twc, int band = 0) {
     using G = ColDir<N2>;
     constexpr int PTS = G::PTS, C = G::C, SPB = G::SPB, R1 = G::R1, R2 = G::R2, M1 = G::M1;
     uint32_t *raw = reinterpret_cast<uint32_t *>(smem_raw);                        // [2][SPB][PTS]
@@ -683,6 +712,7 @@ __device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long l
     float2 *twc = tws + PTS;                                                       // [M1][R1-1]
     float *wins = reinterpret_cast<float *>(twc + G::TWC);                         // [N2][C]
     const int t = threadIdx.x;
+    const size_t zs = p.zstride > 0 ? (size_t)p.zstride : (size_t)p.N;  // scratch spectrum stride
     if (load_twc)
         for (int e = t; e < G::TWC; e += 512) twc[e] = __ldg(p.twA + p.pass[0].off + e);
     // sample (pos e of the tile) of spectrum row rb, times the window value when there is one
@@ -700,9 +730,24 @@ __device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long l
             tws[e] = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
             if (p.win) wins[e] = __ldg(p.coef + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
         }
-        // frames of SPB spectra into raw[buf], 16-byte copies
+        // frames of SPB spectra into raw[buf], 16-byte copies (sub-band input:
+        // 4-byte copies of this band's samples, nsub words apart)
         auto stage = [&](int sb, int buf) {
             const int nbb = min(SPB, s_end - sb);
+            if (p.nsub > 1) {
+                for (int e = t; e < nbb * PTS; e += 512) {
+                    const int u = e / PTS, r = e % PTS;  // r = n2 C + c
+                    const long long fr = s0 + sb + u;
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) +
+                                          (fr * p.N + n1_0 + (long long)p.N1 * (r / C) + r % C) * p.nsub + band;
+                    uint32_t *dst = raw + (buf * SPB + u) * PTS + r;
+                    if (dbg_ok(fr < p.nframes, kDbgInput))
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                                     :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                return;
+            }
             constexpr int per_row = C / 4, per_frame = PTS / 4;
             for (int e = t; e < nbb * per_frame; e += 512) {
                 const int u = e / per_frame, r = e % per_frame;
@@ -734,7 +779,7 @@ __device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long l
 #pragma unroll
                         for (int q = 0; q < N2; q++) v[q] = sample(rb + sb * PTS, q * C + c);
                         Dft<N2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N + n1_0 + c;
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * zs + n1_0 + c;
                         if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
                         z[0] = v[0];
 #pragma unroll
@@ -771,7 +816,7 @@ __device__ __forceinline__ void coldir_tile(const ColParams &p, void *Zc, long l
 #pragma unroll
                         for (int q = 0; q < R2; q++) v[q] = d[q * C];
                         Dft<R2>::run(v);
-                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * p.N +
+                        P2 *z = reinterpret_cast<P2 *>(Zc) + (size_t)(s_base + sb) * zs +
                                 (size_t)(b * R2) * p.N1 + n1_0 + c;
                         if (!dbg_ok(s_base + sb < sc && n1_0 + c < p.N1, kDbgScratch)) continue;
 #pragma unroll
@@ -795,7 +840,13 @@ __global__ void __launch_bounds__(512) fir_coldir_kernel(const __grid_constant__
         const int s_beg = (int)(f - base);
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
-        coldir_tile<N2>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first);
+        if (p.band < 0) {  // every band in this launch: adjacent tiles are the bands of one column tile
+            const int band = x % p.nsub;
+            coldir_tile<N2>(p, reinterpret_cast<P2 *>(p.Z) + (size_t)band * p.N, p.s0, p.sc, x / p.nsub, s_beg, s_end,
+                            smem_raw, first, band);
+        } else {
+            coldir_tile<N2>(p, p.Z, p.s0, p.sc, x, s_beg, s_end, smem_raw, first, p.band);
+        }
         first = false;
     }
 }

@@ -361,7 +361,11 @@ def test_plans_of_different_sizes_coexist():
 
 @pytest.mark.parametrize("cfg", [(4096, 8, 2, PFB, WIN_HANN, 21, 8), (16384, 1, 2, DIRECT, WIN_RECT, 9, 8),
                                  (2048, 8, 1, PFB, WIN_HANN, 13, 8), (65536, 8, 2, PFB, WIN_HANN, 3, 8),
-                                 (1024, 4, 2, PFB, WIN_HAMMING, 40, 3)])
+                                 (1024, 4, 2, PFB, WIN_HAMMING, 40, 3),
+                                 # kernel A reading each band in place: PFB and direct register-column
+                                 # forms, several 32 MiB chunks with a ragged last one
+                                 (65536, 8, 2, PFB, WIN_HANN, 70, 4), (131072, 5, 2, PFB, WIN_HAMMING, 37, 8),
+                                 (524288, 1, 2, DIRECT, WIN_RECT, 19, 2), (65536, 1, 2, DIRECT, WIN_HANN, 45, 8)])
 def test_subband_mode_matches_oracle(oracle_mod, cfg):
     """Eight-sub-band modes (16 FFTs in parallel): input [time][sub][pol][re, im],
     output [sub][channel]; each sub-band equals the oracle on its own samples."""
@@ -379,6 +383,24 @@ def test_subband_mode_matches_oracle(oracle_mod, cfg):
     for b in range(nsub):
         o = run_oracle(oracle_mod, bank, np.ascontiguousarray(x[:, b]))
         assert_close(got[b].reshape(o.shape), o, what=f"{cfg} sub-band {b}")
+
+
+@pytest.mark.parametrize("cfg", [(16384, 8, 2, PFB, WIN_HANN, 70, 3), (16384, 1, 2, DIRECT, WIN_HANN, 50, 5)])
+def test_subband_in_place_band_by_band_matches_oracle(oracle_mod, cfg):
+    """Two-kernel sub-band plans with short columns (no tiled fold): kernel A
+    reads each band in place, one band after another over 32 MiB chunks."""
+    from paper_1411_0436_gb300.vspec import PLAN_TWO_KERNEL, Plan
+    n, p, npol, mode, win, s, nsub = cfg
+    bank = Bank(n, p, npol, mode, win, s, rho=0.3, tones=(Tone(20.0, n * 0.3 + 0.2, (0,)),))
+    x = np.ascontiguousarray(np.stack([workloads.generate(bank, 300 + 7 * b) for b in range(nsub)], axis=1))
+    with Plan(n, p, npol, mode, win, PLAN_TWO_KERNEL, nsub=nsub) as plan:
+        acc = torch.zeros(plan.out_floats, dtype=torch.float32, device="cuda")
+        plan.execute(torch.from_numpy(x.view(np.uint8).reshape(-1)).cuda(), s, acc)
+        torch.cuda.synchronize()
+        got = acc.cpu().numpy().astype(np.float64).reshape(nsub, -1)
+    for b in range(nsub):
+        o = run_oracle(oracle_mod, bank, np.ascontiguousarray(x[:, b]))
+        assert_close(got[b].reshape(o.shape), o, what=f"{cfg} band {b}")
 
 
 @pytest.mark.parametrize("cfg", [(4096, 8, 2, PFB, WIN_HANN, 11), (32768, 8, 2, PFB, WIN_HANN, 30),
