@@ -151,9 +151,14 @@ VSPEC_API vspec_status vspec_plan_get_shape(const vspec_plan *plan, int *col_len
  *   input   int8 [(nspectra + P_eff - 1) * nchan][nsub][npol][re, im]
  *           (the sub-bands of one time sample are adjacent);
  *   output  [nsub][nchan] of float4 (npol == 2) or float (npol == 1).
- * Each call copies chunks of about 64 MiB of input into sub-band-contiguous
- * order in plan-owned scratch, then channelizes every sub-band. nsub == 1 is
- * exactly vspec_plan_create_ex.
+ * Dual-pol plans whose kernel A is a register-column form (PFB of 5..8 taps
+ * or direct mode with 2048-point rows; a fused plan's own two-kernel plan
+ * counts) read each sub-band of the input in place: where the tiled fold
+ * applies (nchan >= 2^15), every sub-band of a chunk runs in one kernel-A
+ * and one kernel-B launch, so the input is read from HBM once; otherwise
+ * sub-band after sub-band over chunks of about 32 MiB of input. Other plans
+ * copy chunks of about 64 MiB of input into sub-band-contiguous order in
+ * plan-owned scratch first. nsub == 1 is exactly vspec_plan_create_ex.
  */
 VSPEC_API vspec_status vspec_plan_create_sb(vspec_plan **out, int nchan, int ntaps, int npol, int nsub,
                                             vspec_mode mode, vspec_window window, unsigned flags);
