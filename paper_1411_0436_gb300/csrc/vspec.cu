@@ -940,8 +940,10 @@ vspec_status build_plan(vspec_plan *p) {
     if (p->tc_int8) {  // the per-column B blocks: N1 columns x Q residues x P taps x 2 KiB (x terms)
         if ((st = dev_alloc((void **)&p->dftop, (size_t)N1 * (N2 / 16) * p->P * p->bterms * 2048, &tot)))
             return st;
-    } else if (p->tc_cols) {  // the column DFT operand F, hi and lo
-        if ((st = dev_alloc((void **)&p->dftop, (size_t)2 * (2 * N2) * (2 * N2) * 2, &tot))) return st;
+    } else if (p->tc_cols) {  // the column DFT operand F, hi and lo, then the scaled four-step twiddles
+        if ((st = dev_alloc((void **)&p->dftop, (size_t)2 * (2 * N2) * (2 * N2) * 2 + (size_t)N * sizeof(float2),
+                            &tot)))
+            return st;
     }
     if (p->kahan) {
         if ((st = dev_alloc(&p->partial_comp, (size_t)p->slots_cap * N * accel, &tot))) return st;
@@ -971,8 +973,11 @@ vspec_status build_plan(vspec_plan *p) {
             if (ps.m * (ps.r - 1) > 0)
                 vspec::gen_pass_tw_kernel<<<(ps.m * (ps.r - 1) + 255) / 256, 256, 0, s0>>>(p->twB, ps);
         vspec::gen_twz_kernel<<<(N + 255) / 256, 256, 0, s0>>>(p->twZ, N, N1, N2, d_kA);
-        if (p->tc_cols && !p->tc_int8)
+        if (p->tc_cols && !p->tc_int8) {
             vspec::gen_coltc_operand_kernel<<<(4 * N2 * N2 + 255) / 256, 256, 0, s0>>>(p->dftop, N2);
+            vspec::gen_coltc_twz_kernel<<<(N + 255) / 256, 256, 0, s0>>>(
+                reinterpret_cast<float2 *>(p->dftop + (size_t)2 * (2 * N2) * (2 * N2) * 2), p->twZ, N, N1, N2);
+        }
         if (p->tc_int8) {
             const long long nb = (long long)N1 * (N2 / 16) * p->P * 1024;
             vspec::gen_tcfir_operand_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s0>>>(p->dftop, p->coef, N, N1,

@@ -79,7 +79,8 @@ struct ColParams {
     int G;               // tiles per group (tile_split); 0 or 1: no groups
     int win;             // direct mode with a window: multiply by coef (register-column kernels)
     // tensor-core column kernel only
-    const unsigned char *dftop;  // the column DFT operand: fp16 hi part, then lo part
+    const unsigned char *dftop;  // the column DFT operand: fp16 hi part, then lo part (then, for
+                                 // fir_coltc_kernel, the four-step twiddles times 2^-12)
     int *status;                 // set to 1 if a bounded wait for the tensor cores gave up
     unsigned wait_limit;         // polls of that wait
     int bterms;                  // fp16 parts of the fused tensor-core operand: 1 (hi) or 2 (hi, lo)

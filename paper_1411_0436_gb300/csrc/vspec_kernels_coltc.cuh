@@ -14,14 +14,19 @@
 //   F[2n2+1][2k2+1] = cos  of 2 pi n2 k2 / N2,
 //
 // so D's row holds sum_n2 y[n1 + N1 n2] W_N2^(n2 k2) in natural k2 order
-// (times a power of two, kColTc*, that keeps the fp16 low parts normal). D
-// has two buffers in tensor memory, each as two accumulators (the two halves
-// of the K slices, added in FP32 by the epilogue): the epilogue of one batch
-// runs while the tensor cores compute the next.
+// (times a power of two, kColTc*, that keeps the fp16 low parts normal).
+// Y has two buffers in shared memory and D two in tensor memory: while the
+// tensor cores compute batch b, the CUDA cores run the epilogue of batch
+// b - 1 and then pre-filter batch b + 1 into the other Y buffer, so the
+// products are off the critical path.
 // Y and F are split into fp16 high and low parts (x = hi + lo, hi =
 // fp16(x), lo = fp16(x - hi)) and three tcgen05.mma terms, Y_hi F_hi +
 // Y_lo F_hi + Y_hi F_lo, accumulate in FP32 in tensor memory: about 22
 // significant bits of each operand (the dropped Y_lo F_lo is below 2^-22).
+// The two small terms are issued first and the large Y_hi F_hi last: the
+// tensor cores' FP32 accumulation loses low bits relative to the running
+// sum, so the small terms are summed while it is still small, and only the
+// last K / 16 steps add at full magnitude.
 // Both low parts matter: an emulation of this stage with Y rounded to fp16
 // alone gives 9e-4 of the spectrum RMS on a one-spectrum dump of the
 // 131072-channel workload, with F rounded to fp16 hi + lo alone 4e-6.
@@ -30,7 +35,10 @@
 // signals an mbarrier that the CTA waits on with a bounded spin (status word
 // and a clean exit if it gives up). Each thread then reads one row of D with
 // tcgen05.ld (its 16 outputs of one polarisation), multiplies by W_N^(n1 k2)
-// and writes its polarisation's half of each scratch element: this kernel's
+// (a copy of the four-step twiddles scaled by 2^-12, read through L1; the
+// tile's coefficients stay in registers: shared memory holds only the
+// operands and the staged frames) and writes its polarisation's half of each
+// scratch element: this kernel's
 // scratch elements hold (X.re, X.im, Y.re, Y.im), and the 2048-point row
 // kernel reads them in that order (its ZSPLIT form).
 //
@@ -69,13 +77,10 @@ struct ColTc {
     static constexpr int BPART = NN * K * 2;       // bytes of one fp16 part of F
     static constexpr int KSTEPS = K / 16;
     static constexpr int TMEM_COLS = MB * NN;      // fp32 columns of one D buffer (two are allocated)
-    // Y hi, Y lo, F hi, F lo, raw frames [2][SPB][PTS] u32, coefficients
-    // [PT][PTS] float, twiddle tile [N2][C] float2
-    static constexpr size_t smem = 2 * (size_t)APART + 2 * (size_t)BPART + 2 * (size_t)SPB * PTS * 4 +
-                                   (size_t)PT * PTS * 4 + (size_t)PTS * 8;
+    // two A buffers (Y hi, Y lo), F hi, F lo, raw frames [2][SPB][PTS] u32
+    static constexpr size_t smem = 4 * (size_t)APART + 2 * (size_t)BPART + 2 * (size_t)SPB * PTS * 4;
     static_assert(N2 == 16 || N2 == 32 || N2 == 64, "column lengths of this kernel");
-    static_assert(MB * 128 == ROWS && TMEM_COLS == 128, "2 x 2 accumulators of 128 TMEM columns, whole M blocks");
-    static_assert(KSTEPS % 2 == 0, "two halves of the K slices");
+    static_assert(MB * 128 == ROWS && TMEM_COLS == 128, "2 accumulators of 128 TMEM columns, whole M blocks");
     // Thread t pre-filters point (n2, c) of the tile, laid out so that every
     // warp holds 8 consecutive columns x 4 consecutive n2: its stores of Y
     // then fill 8 rows x 4 words of one core matrix, free of bank conflicts.
@@ -116,6 +121,30 @@ __global__ void gen_coltc_operand_kernel(unsigned char *op, int N2) {
     *reinterpret_cast<__half *>(op + NN * K * 2 + o) = lo;
 }
 
+// The four-step twiddles W_N^(n1 k2) times 2^-12 (exact) for the epilogue of
+// fir_coltc_kernel, stored after F in the plan's operand array, tile by tile:
+// entry x * 512 + k2 * C + c is column n1 = x * C + c of tile x (C = 512 /
+// N2), so that a tile's twiddles are one contiguous 4 KiB block in L1.
+__global__ void gen_coltc_twz_kernel(float2 *dst, const float2 *twZ, int N, int N1, int N2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int C = 512 / N2, x = e / 512, r = e % 512, k2 = r / C, c = r % C;
+    const float2 w = twZ[(size_t)k2 * N1 + x * C + c];
+    dst[e] = make_float2(w.x * kColTcUnscale, w.y * kColTcUnscale);
+}
+
+// L1 policy of the epilogue: the chunk-scratch stores (64 KiB per batch)
+// must not evict the tile's twiddles from the small L1 that the operands
+// leave, so they do not allocate there, and the twiddle loads are kept last.
+__device__ __forceinline__ void st_no_l1(float2 *ptr, float2 v) {
+    asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(ptr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float2 ld_keep_l1(const float2 *ptr) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
+    return v;
+}
+
 // hi/lo fp16 split of a complex value as two packed half2 words (re, im)
 __device__ __forceinline__ void split_half2(float re, float im, uint32_t &hi, uint32_t &lo) {
     const __half2 h = __floats2half2_rn(re, im);
@@ -137,23 +166,24 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     using namespace tc;
     constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
     extern __shared__ __align__(128) unsigned char smem_ct[];
-    unsigned char *ahi = smem_ct, *alo = ahi + G::APART;
-    unsigned char *fhi = alo + G::APART, *flo = fhi + G::BPART;
+    // A buffer b: hi part at smem_ct + 2 b APART, lo part APART further on
+    unsigned char *fhi = smem_ct + 4 * G::APART, *flo = fhi + G::BPART;
     uint32_t *raw = reinterpret_cast<uint32_t *>(flo + G::BPART);  // [2][SPB][PTS]
-    float *cfs = reinterpret_cast<float *>(raw + 2 * SPB * PTS);     // [PT][PTS]
-    float2 *tws = reinterpret_cast<float2 *>(cfs + PT * PTS);        // [N2][C]
-    __shared__ __align__(8) uint64_t mbar;
+    // W_N^(n1 k2) * 2^-12 in natural k2 order, [tile][k2][c] (after F in the operand array)
+    const float2 *twsc = reinterpret_cast<const float2 *>(p.dftop + 2 * G::BPART);
+    __shared__ __align__(8) uint64_t mbar[2];  // MMA completion of the batches in D buffer 0 / 1
     __shared__ uint32_t tmem_slot;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int D = PT - p.P;  // leading zero taps
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_addr(&tmem_slot)), "r"(4u * G::TMEM_COLS) : "memory");
+                     :: "r"(smem_addr(&tmem_slot)), "r"(2u * G::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        mbar_init(&mbar, 1);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // F (hi and lo) into shared memory, 16 bytes at a time
@@ -172,7 +202,11 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     const int n2 = G::pt_n2(t), c = G::pt_c(t);  // the point this thread pre-filters
 
     bool ok = true;
-    uint32_t batches = 0;  // MMA batches committed (mbarrier phase, TMEM buffer)
+    // Batch gi (counted over the CTA's tiles) uses A buffer and D buffer gi & 1
+    // and is the (gi >> 1)-th commit on mbar[gi & 1]. Batch gi - 2 is waited
+    // for before batch gi writes its A buffer, so the waits on each mbarrier
+    // alternate with its commits and the phase parity is never ambiguous.
+    uint32_t gi = 0;
     const TileSplit sp = tile_split(p.tiles, p.sc, p.G);
     for (long long f = sp.lo; f < sp.hi && ok;) {
         const long long base = f / p.sc * p.sc;  // first item of this super-tile
@@ -181,16 +215,12 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
         const int n1_0 = x * C;
-        // W_N^(n1 k2) in natural k2 order, times 2^-kScale (undoes the
-        // operands' power-of-two scaling exactly)
-        for (int e = t; e < PTS; e += blockDim.x) {  // tws[k2 C + c]
-            const float2 w = __ldg(p.twZ + (size_t)(e / C) * p.N1 + n1_0 + (e % C));
-            tws[e] = make_float2(w.x * kColTcUnscale, w.y * kColTcUnscale);
-        }
         const long long n_pt = n1_0 + c + (long long)p.N1 * n2;
+        // this point's coefficients (times 2^4), kept in registers for the tile
+        float2 cf2[PT];
 #pragma unroll
         for (int k = 0; k < PT; k++)
-            cfs[k * PTS + t] = k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) * kColTcYScale : 0.f;
+            cf2[k] = dup2(k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) * kColTcYScale : 0.f);
         P2 win[PT];
         const long long sabs = p.s0 + s_beg;
 #pragma unroll
@@ -214,41 +244,51 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
-        // epilogue of a finished batch: this thread's row of D (TMEM buffer
-        // dbuf, the sum of its two K halves), 16 outputs k2 = k0 .. k0 + 15 of
-        // polarisation ep, column ec, spectrum eu of the batch, times
-        // W_N^(n1 k2), into the scratch
-        auto epilogue = [&](int sbase, int nbb, uint32_t dbuf) {
-            float d[32], d1[32];
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + 2u * dbuf * G::TMEM_COLS + (uint32_t)(32 * g);
-            tmem_ld32(ta, d);
-            tmem_ld32(ta + G::TMEM_COLS, d1);
-#pragma unroll
-            for (int i = 0; i < 32; i++) d[i] += d1[i];
-            if (eu < nbb) {
+        // Wait for batch bi's MMAs (warp-uniform answer), then its epilogue:
+        // this thread's row of D buffer bi & 1, 16 outputs k2 = k0 .. k0 + 15 of polarisation ep, column ec,
+        // spectrum eu of the batch, times W_N^(n1 k2), into the scratch.
+        // tcgen05.ld is warp-collective: every lane loads, lanes past the
+        // batch's spectra skip the stores.
+        auto finish = [&](int sbase, int nbb, uint32_t bi) {
+            bool done = mbar_wait(&mbar[bi & 1u], (bi >> 1) & 1u, p.wait_limit);
+            done = __all_sync(0xffffffffu, done);
+            if (done) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (bi & 1u) * G::TMEM_COLS + (uint32_t)(32 * g);
                 float2 *z = reinterpret_cast<float2 *>(reinterpret_cast<P2 *>(p.Z) + (size_t)(sbase + eu) * p.N +
                                                        n1_0 + ec) + ep;
+                const float2 *w = twsc + (size_t)x * PTS + ec;
+                float dd[2][16];
+                tmem_ld16x2(ta, ta + 16u, dd[0], dd[1]);
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int k2 = k0 + j;
-                    z[(size_t)k2 * p.N1 * 2] = cmul(make_float2(d[2 * j], d[2 * j + 1]), tws[k2 * C + ec]);
+                for (int h = 0; h < 2; h++) {
+                    const float (&d)[16] = dd[h];
+                    if (eu < nbb) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const int k2 = k0 + 8 * h + j;
+                            st_no_l1(z + (size_t)k2 * p.N1 * 2, cmul(make_float2(d[2 * j], d[2 * j + 1]), ld_keep_l1(w + k2 * C)));
+                        }
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            return done;
         };
-        int pend_base = 0, pend_nb = 0;  // the batch whose MMAs are done and epilogue pending
+        int pend_base = 0, pend_nb = 0;  // the batch issued last, its epilogue pending
         stage(s_beg, 0);
         for (int s_base = s_beg, buf = 0; s_base < s_end; s_base += SPB, buf ^= 1) {
             const int nb = min(SPB, s_end - s_base);
             asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();  // frames visible; the other buffer is free
+            // frames visible; the other frame buffer is free; the epilogue of
+            // batch gi - 2 is done with D buffer gi & 1 and its MMAs with A
+            // buffer gi & 1; every thread's waits so far succeeded
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
             if (s_base + SPB < s_end) stage(s_base + SPB, buf ^ 1);
-            float2 cf2[PT];
-#pragma unroll
-            for (int k = 0; k < PT; k++) cf2[k] = dup2(cfs[k * PTS + t]);
+            const uint32_t ab = gi & 1u;
+            unsigned char *ahi = smem_ct + 2 * ab * G::APART, *alo = ahi + G::APART;
             // FIR of spectrum u of the batch into rows (2u + p) C + c of Y, K = 2 n2
-            // (the previous batch's MMAs are done with Y: their wait ended the
-            // previous iteration)
             auto fir_one = [&](auto uc) {
                 constexpr int u = decltype(uc)::value;
                 constexpr int snew = (u + PT - 1) % PT;
@@ -273,60 +313,52 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             if (nb == SPB) for_slots(fir_one, std::make_integer_sequence<int, SPB>{});
             else for_slots_below(fir_one, nb, std::make_integer_sequence<int, SPB>{});
             // Y is complete: make it visible to the tensor cores, then issue
-            // into TMEM buffer batches & 1 (the other buffer holds the pending batch)
+            // batch gi into D buffer ab
             fence_proxy_async();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dbuf = batches & 1u;
             if (t == 0) {
                 constexpr uint32_t idesc = instr_desc_f16(128, G::NN);
-                const unsigned char *as[3] = {ahi, alo, ahi};
-                const unsigned char *bs[3] = {fhi, fhi, flo};
-                // each half of the K slices accumulates in its own TMEM
-                // columns (shorter accumulation chains in the tensor cores);
-                // the epilogue adds the halves in FP32
+                // small terms first: Y_lo F_hi, Y_hi F_lo, then Y_hi F_hi
+                const unsigned char *as[3] = {alo, ahi, ahi};
+                const unsigned char *bs[3] = {fhi, flo, fhi};
 #pragma unroll
                 for (int m = 0; m < G::MB; m++) {
+                    uint32_t acc = 0;
+                    const uint32_t dcol = tmem + ab * G::TMEM_COLS + (uint32_t)(m * G::NN);
 #pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        uint32_t acc = 0;
-                        const uint32_t dcol = tmem + (2u * dbuf + hh) * G::TMEM_COLS + (uint32_t)(m * G::NN);
+                    for (int term = 0; term < 3; term++) {
 #pragma unroll
-                        for (int term = 0; term < 3; term++) {
-#pragma unroll
-                            for (int ks = hh * G::KSTEPS / 2; ks < (hh + 1) * G::KSTEPS / 2; ks++) {
-                                const uint64_t ad = smem_desc(smem_addr(as[term]) + m * 16 * G::SBO + 256u * ks, 128u, G::SBO);
-                                const uint64_t bd = smem_desc(smem_addr(bs[term]) + 256u * ks, 128u, G::SBO);
-                                mma_bf16(dcol, ad, bd, idesc, acc);
-                                acc = 1;
-                            }
+                        for (int ks = 0; ks < G::KSTEPS; ks++) {
+                            const uint64_t ad = smem_desc(smem_addr(as[term]) + m * 16 * G::SBO + 256u * ks, 128u, G::SBO);
+                            const uint64_t bd = smem_desc(smem_addr(bs[term]) + 256u * ks, 128u, G::SBO);
+                            mma_bf16(dcol, ad, bd, idesc, acc);
+                            acc = 1;
                         }
                     }
                 }
-                mma_commit(&mbar);
+                mma_commit(&mbar[ab]);
             }
             // the previous batch's epilogue runs while the tensor cores work
-            if (pend_nb > 0) epilogue(pend_base, pend_nb, dbuf ^ 1u);
-            const bool done = mbar_wait(&mbar, dbuf, p.wait_limit);
-            batches++;
-            ok = __syncthreads_and(done);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok) break;
+            // on this one (and this batch's while the next one is pre-filtered)
+            if (pend_nb > 0) ok = finish(pend_base, pend_nb, gi - 1);
             pend_base = s_base;
             pend_nb = nb;
+            gi++;
         }
-        if (ok && pend_nb > 0) epilogue(pend_base, pend_nb, (batches - 1) & 1u);
-        __syncthreads();  // the batches are done with the twiddle tile and D
+        if (ok && pend_nb > 0) ok = finish(pend_base, pend_nb, gi - 1);
+        ok = __syncthreads_and(ok);  // the tile's batches are done with D and A
     }
     if (!ok && t == 0) atomicExch(p.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        // a batch whose wait gave up has MMAs outstanding: wait for its commit
-        // with the full bound before freeing their tensor memory
-        if (!ok) mbar_wait(&mbar, (batches - 1) & 1u);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(4u * G::TMEM_COLS) : "memory");
+        // after a wait that gave up, MMAs may be outstanding: wait with the
+        // full bound for the last batch's commit (it arrives once every MMA
+        // issued before it is complete) before freeing their tensor memory
+        if (!ok && gi > 0) mbar_wait(&mbar[(gi - 1) & 1u], ((gi - 1) >> 1) & 1u);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2u * G::TMEM_COLS) : "memory");
     }
 }
 
