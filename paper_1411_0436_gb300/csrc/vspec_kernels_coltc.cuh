@@ -35,10 +35,11 @@
 // signals an mbarrier that the CTA waits on with a bounded spin (status word
 // and a clean exit if it gives up). Each thread then reads one row of D with
 // tcgen05.ld (its 16 outputs of one polarisation), multiplies by W_N^(n1 k2)
-// (a copy of the four-step twiddles scaled by 2^-12, read through L1; the
-// tile's coefficients stay in registers: shared memory holds only the
-// operands and the staged frames) and writes its polarisation's half of each
-// scratch element: this kernel's
+// (a copy of the four-step twiddles scaled by 2^-12, loaded once per tile
+// into free columns of the thread's own tensor-memory lane and read back
+// beside D; the tile's coefficients stay in registers: shared memory holds
+// only the operands and the staged frames) and writes its polarisation's
+// half of each scratch element: this kernel's
 // scratch elements hold (X.re, X.im, Y.re, Y.im), and the 2048-point row
 // kernel reads them in that order (its ZSPLIT form).
 //
@@ -76,11 +77,16 @@ struct ColTc {
     static constexpr int APART = ROWS * K * 2;     // bytes of one fp16 part of Y
     static constexpr int BPART = NN * K * 2;       // bytes of one fp16 part of F
     static constexpr int KSTEPS = K / 16;
-    static constexpr int TMEM_COLS = MB * NN;      // fp32 columns of one D buffer (two are allocated)
+    static constexpr int TMEM_COLS = MB * NN;      // fp32 columns of one D buffer
+    // tensor memory: D buffers 0 and 1, then each epilogue thread's 16
+    // twiddles (32 columns per thread column group g, 4 groups)
+    static constexpr int TMEM_ALLOC = 4 * TMEM_COLS;
     // two A buffers (Y hi, Y lo), F hi, F lo, raw frames [2][SPB][PTS] u32
     static constexpr size_t smem = 4 * (size_t)APART + 2 * (size_t)BPART + 2 * (size_t)SPB * PTS * 4;
     static_assert(N2 == 16 || N2 == 32 || N2 == 64, "column lengths of this kernel");
+    static_assert(C % 8 == 0 && SPB % 4 == 0 && PTS % 4 == 0, "whole core-matrix row groups, whole copy rounds");
     static_assert(MB * 128 == ROWS && TMEM_COLS == 128, "2 accumulators of 128 TMEM columns, whole M blocks");
+    static_assert(2 * TMEM_COLS + 4 * 32 <= TMEM_ALLOC, "twiddle columns after the accumulators");
     // Thread t pre-filters point (n2, c) of the tile, laid out so that every
     // warp holds 8 consecutive columns x 4 consecutive n2: its stores of Y
     // then fill 8 rows x 4 words of one core matrix, free of bank conflicts.
@@ -133,25 +139,32 @@ __global__ void gen_coltc_twz_kernel(float2 *dst, const float2 *twZ, int N, int 
     dst[e] = make_float2(w.x * kColTcUnscale, w.y * kColTcUnscale);
 }
 
-// L1 policy of the epilogue: the chunk-scratch stores (64 KiB per batch)
-// must not evict the tile's twiddles from the small L1 that the operands
-// leave, so they do not allocate there, and the twiddle loads are kept last.
+// The chunk-scratch stores of the epilogue (64 KiB per batch, never read
+// back by this kernel) do not allocate in L1.
 __device__ __forceinline__ void st_no_l1(float2 *ptr, float2 v) {
     asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(ptr), "f"(v.x), "f"(v.y) : "memory");
 }
-__device__ __forceinline__ float2 ld_keep_l1(const float2 *ptr) {
-    float2 v;
-    asm volatile("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
-    return v;
-}
 
-// hi/lo fp16 split of a complex value as two packed half2 words (re, im)
-__device__ __forceinline__ void split_half2(float re, float im, uint32_t &hi, uint32_t &lo) {
-    const __half2 h = __floats2half2_rn(re, im);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
-    hi = *reinterpret_cast<const uint32_t *>(&h);
-    lo = *reinterpret_cast<const uint32_t *>(&l);
+// hi/lo fp16 split of both polarisations of a complex value, y = (re, im)
+// with re = (X.re, Y.re), im = (X.im, Y.im), into packed half2 words (re,
+// im) per polarisation. The high part is y with its mantissa truncated to
+// fp16's 11 significant bits (exact in fp16 for the operands' range), so the
+// low part y - hi is exact in FP32 and then rounds once to fp16: |lo| <
+// 2^-10 |y|, hi + lo within 2^-21 |y| of y. On the packed pairs this takes
+// four bit masks, two paired subtractions and four conversions.
+__device__ __forceinline__ void split_p2(const P2 &y, uint32_t &hx, uint32_t &lx, uint32_t &hy, uint32_t &ly) {
+    constexpr unsigned kMask = 0xFFFFE000u;
+    const float2 hr = make_float2(__uint_as_float(__float_as_uint(y.re.x) & kMask),
+                                  __uint_as_float(__float_as_uint(y.re.y) & kMask));
+    const float2 hi = make_float2(__uint_as_float(__float_as_uint(y.im.x) & kMask),
+                                  __uint_as_float(__float_as_uint(y.im.y) & kMask));
+    const float2 lr = sub2(y.re, hr), li = sub2(y.im, hi);
+    const __half2 a = __floats2half2_rn(hr.x, hi.x), b = __floats2half2_rn(hr.y, hi.y);
+    const __half2 c = __floats2half2_rn(lr.x, li.x), d = __floats2half2_rn(lr.y, li.y);
+    hx = *reinterpret_cast<const uint32_t *>(&a);
+    hy = *reinterpret_cast<const uint32_t *>(&b);
+    lx = *reinterpret_cast<const uint32_t *>(&c);
+    ly = *reinterpret_cast<const uint32_t *>(&d);
 }
 
 // fp16 instruction descriptor of kind::f16: fp32 D (bits 4-5 = 1), fp16 A and
@@ -165,6 +178,10 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     using G = ColTc<N2>;
     using namespace tc;
     constexpr int PT = G::PT, PTS = G::PTS, C = G::C, SPB = G::SPB;
+    // the plan uses this kernel only with 2048-point rows: the transform
+    // length and row stride are compile-time constants (immediate offsets)
+    constexpr int N1 = 2048;
+    constexpr long long NCH = (long long)N1 * N2;
     extern __shared__ __align__(128) unsigned char smem_ct[];
     // A buffer b: hi part at smem_ct + 2 b APART, lo part APART further on
     unsigned char *fhi = smem_ct + 4 * G::APART, *flo = fhi + G::BPART;
@@ -178,7 +195,7 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_addr(&tmem_slot)), "r"(2u * G::TMEM_COLS) : "memory");
+                     :: "r"(smem_addr(&tmem_slot)), "r"((uint32_t)G::TMEM_ALLOC) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
@@ -200,6 +217,14 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     const int R = mb * 128 + 32 * q + lane;  // row of Y this thread reads back
     const int ec = R % C, ep = (R / C) & 1, eu = R / (2 * C);
     const int n2 = G::pt_n2(t), c = G::pt_c(t);  // the point this thread pre-filters
+    // its operand offset for spectrum u, polarisation pol of a batch is
+    // o_y + (2 u + pol) (C / 8) SBO (rows (2 u + pol) C + c, C a multiple of 8)
+    const int o_y = G::off(c, 2 * n2);
+    // its share of the frame staging: 16-byte copies e = t + PTS i, i < SPB / 4,
+    // of frame u = t / (PTS / 4) + 4 i, tile row rn2, columns 4 ch .. 4 ch + 3
+    constexpr int per_row = C / 4, per_frame = PTS / 4;
+    const int st_u = t / per_frame, st_r = t % per_frame, st_n2 = st_r / per_row, st_ch = st_r % per_row;
+    const int st_dst = st_u * PTS + G::pt_index(st_n2, st_ch * 4);
 
     bool ok = true;
     // Batch gi (counted over the CTA's tiles) uses A buffer and D buffer gi & 1
@@ -215,33 +240,48 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
         const int s_end = (int)(min(sp.hi, base + p.sc) - base);
         f = base + s_end;
         const int n1_0 = x * C;
-        const long long n_pt = n1_0 + c + (long long)p.N1 * n2;
+        const long long n_pt = n1_0 + c + (long long)N1 * n2;
         // this point's coefficients (times 2^4), kept in registers for the tile
         float2 cf2[PT];
 #pragma unroll
         for (int k = 0; k < PT; k++)
-            cf2[k] = dup2(k >= D ? __ldg(p.coef + (size_t)(k - D) * p.N + n_pt) * kColTcYScale : 0.f);
+            cf2[k] = dup2(k >= D ? __ldg(p.coef + (size_t)(k - D) * NCH + n_pt) * kColTcYScale : 0.f);
         P2 win[PT];
         const long long sabs = p.s0 + s_beg;
 #pragma unroll
         for (int k = 0; k < PT - 1; k++) {
             long long fr = sabs - D + k;
             if (fr < 0) fr = 0;
-            win[k] = unpack_p2(load_raw<2>(p.in, fr * p.N + n_pt) ^ 0x80808080u);
+            win[k] = unpack_p2(load_raw<2>(p.in, fr * NCH + n_pt) ^ 0x80808080u);
         }
+        // this thread's epilogue twiddles W_N^(n1 k2) 2^-12, k2 = k0 .. k0 + 15 of
+        // column ec, into its TMEM lane (the previous tile's epilogues are done
+        // with them: the barrier that ended that tile)
+        const uint32_t ttw = tmem + ((uint32_t)(32 * q) << 16) + 2u * G::TMEM_COLS + (uint32_t)(32 * g);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            float w[16];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const float2 v = __ldg(twsc + (size_t)x * PTS + (k0 + 8 * h + j) * C + ec);
+                w[2 * j] = v.x;
+                w[2 * j + 1] = v.y;
+            }
+            tmem_st16_wait(ttw + 16u * h, w);
+        }
+        // frames of the tile, from spectrum 0 of the chunk on (newest frame
+        // of each spectrum: P - 1 frames after the spectrum's first)
+        const uint32_t *st_src = reinterpret_cast<const uint32_t *>(p.in) + (p.s0 + st_u + p.P - 1) * NCH + n1_0 +
+                                 (long long)N1 * st_n2 + st_ch * 4;
         auto stage = [&](int sb, int buf) {
             const int nbb = min(SPB, s_end - sb);
-            constexpr int per_row = C / 4, per_frame = PTS / 4;
-            for (int e = t; e < nbb * per_frame; e += blockDim.x) {
-                const int u = e / per_frame, r = e % per_frame;
-                const int rn2 = r / per_row, ch = r % per_row;
-                const long long fr = p.s0 + sb + u + p.P - 1;
-                const uint32_t *src = reinterpret_cast<const uint32_t *>(p.in) + fr * p.N + n1_0 +
-                                      (long long)p.N1 * rn2 + ch * 4;
-                uint32_t *dst = raw + (buf * SPB + u) * PTS + G::pt_index(rn2, ch * 4);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
-            }
+            const uint32_t *src = st_src + (long long)sb * NCH;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(raw + buf * SPB * PTS + st_dst);
+#pragma unroll
+            for (int i = 0; i < SPB / 4; i++)
+                if (st_u + 4 * i < nbb)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                 :: "r"(dst + 16u * PTS * i), "l"(src + 4 * i * NCH) : "memory");
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         // Wait for batch bi's MMAs (warp-uniform answer), then its epilogue:
@@ -255,19 +295,18 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             if (done) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (bi & 1u) * G::TMEM_COLS + (uint32_t)(32 * g);
-                float2 *z = reinterpret_cast<float2 *>(reinterpret_cast<P2 *>(p.Z) + (size_t)(sbase + eu) * p.N +
+                float2 *z = reinterpret_cast<float2 *>(reinterpret_cast<P2 *>(p.Z) + (size_t)(sbase + eu) * NCH +
                                                        n1_0 + ec) + ep;
-                const float2 *w = twsc + (size_t)x * PTS + ec;
-                float dd[2][16];
-                tmem_ld16x2(ta, ta + 16u, dd[0], dd[1]);
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const float (&d)[16] = dd[h];
+                    float d[16], w[16];  // 8 outputs and their twiddles
+                    tmem_ld16x2(ta + 16u * h, ttw + 16u * h, d, w);
                     if (eu < nbb) {
 #pragma unroll
                         for (int j = 0; j < 8; j++) {
                             const int k2 = k0 + 8 * h + j;
-                            st_no_l1(z + (size_t)k2 * p.N1 * 2, cmul(make_float2(d[2 * j], d[2 * j + 1]), ld_keep_l1(w + k2 * C)));
+                            st_no_l1(z + (size_t)k2 * N1 * 2, cmul(make_float2(d[2 * j], d[2 * j + 1]),
+                                                                   make_float2(w[2 * j], w[2 * j + 1])));
                         }
                     }
                 }
@@ -302,9 +341,9 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
                     y.im = __ffma2_rn(cf2[k], wk.im, y.im);
                 }
                 uint32_t hx, lx, hy, ly;
-                split_half2(y.re.x, y.im.x, hx, lx);
-                split_half2(y.re.y, y.im.y, hy, ly);
-                const int ox = G::off((2 * u) * C + c, 2 * n2), oy = G::off((2 * u + 1) * C + c, 2 * n2);
+                split_p2(y, hx, lx, hy, ly);
+                constexpr int ou = 2 * u * (C / 8) * G::SBO;
+                const int ox = o_y + ou, oy = o_y + ou + (C / 8) * G::SBO;
                 *reinterpret_cast<uint32_t *>(ahi + ox) = hx;
                 *reinterpret_cast<uint32_t *>(alo + ox) = lx;
                 *reinterpret_cast<uint32_t *>(ahi + oy) = hy;
@@ -358,7 +397,7 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
         // full bound for the last batch's commit (it arrives once every MMA
         // issued before it is complete) before freeing their tensor memory
         if (!ok && gi > 0) mbar_wait(&mbar[(gi - 1) & 1u], ((gi - 1) >> 1) & 1u);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2u * G::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"((uint32_t)G::TMEM_ALLOC) : "memory");
     }
 }
 
