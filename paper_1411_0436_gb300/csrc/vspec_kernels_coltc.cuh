@@ -8,7 +8,8 @@
 // spectra are then one dense real matrix product per 128 rows:
 //
 //   D (rows x 2 N2) = Y (rows x 2 N2) . F (2 N2 x 2 N2),
-//   row = (spectrum u, polarisation p, column c) = (2 u + p) C + c,
+//   row = 8 (2 (u C/8 + c/8) + p) + c % 8  (spectrum u, polarisation p, column c:
+//   the two polarisations of 8 columns in consecutive 8-row groups),
 //   K index 2 n2 + {0: re, 1: im},  N index 2 k2 + {0: re, 1: im},
 //   F[2n2][2k2] = cos, F[2n2][2k2+1] = -sin, F[2n2+1][2k2] = sin,
 //   F[2n2+1][2k2+1] = cos  of 2 pi n2 k2 / N2,
@@ -33,15 +34,16 @@
 // FIR outputs stay below 2^9 in magnitude and the DFT coefficients below 1,
 // well inside fp16's range. One thread issues the MMAs; tcgen05.commit
 // signals an mbarrier that the CTA waits on with a bounded spin (status word
-// and a clean exit if it gives up). Each thread then reads one row of D with
-// tcgen05.ld (its 16 outputs of one polarisation), multiplies by W_N^(n1 k2)
-// (a copy of the four-step twiddles scaled by 2^-12, loaded once per tile
-// into free columns of the thread's own tensor-memory lane and read back
-// beside D; the tile's coefficients stay in registers: shared memory holds
-// only the operands and the staged frames) and writes its polarisation's
-// half of each scratch element: this kernel's
-// scratch elements hold (X.re, X.im, Y.re, Y.im), and the 2048-point row
-// kernel reads them in that order (its ZSPLIT form).
+// and a clean exit if it gives up). The epilogue reads D with the .16x256b
+// shape of tcgen05.ld, which gives each thread two adjacent columns (re, im
+// of one output) of two rows 8 apart: by the row order above, the X and Y
+// polarisations of the same output. It multiplies them by W_N^(n1 k2) (a copy
+// of the four-step twiddles scaled by 2^-12, loaded once per tile into free
+// columns of the thread's own tensor-memory lane and read back beside D; the
+// tile's coefficients stay in registers: shared memory holds only the
+// operands and the staged frames) and writes whole 16-byte scratch elements
+// (X.re, X.im, Y.re, Y.im), the order in which the 2048-point row kernel
+// reads them (its ZSPLIT form).
 //
 // Shared-memory operands (K-major, no swizzle): 8-row x 16-byte core
 // matrices, element (row r, k) at byte
@@ -141,8 +143,9 @@ __global__ void gen_coltc_twz_kernel(float2 *dst, const float2 *twZ, int N, int 
 
 // The chunk-scratch stores of the epilogue (64 KiB per batch, never read
 // back by this kernel) do not allocate in L1.
-__device__ __forceinline__ void st_no_l1(float2 *ptr, float2 v) {
-    asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(ptr), "f"(v.x), "f"(v.y) : "memory");
+__device__ __forceinline__ void st_no_l1(float4 *ptr, float4 v) {
+    asm volatile("st.global.L1::no_allocate.v4.f32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(ptr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
 
 // hi/lo fp16 split of both polarisations of a complex value, y = (re, im)
@@ -211,15 +214,24 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    // the epilogue's share of D: lane quarter q of TMEM, 32 columns from 32 g
+    // The epilogue's share of D: lane quarter q of TMEM, the 32 columns from
+    // 32 g (M block mb, outputs k2 = k0 .. k0 + 15), read as two 16-lane
+    // halves h. Half h holds the 8-row groups 16 mb + 4 q + 2 h (X) and + 1
+    // (Y) of spectrum eu[h], columns 8 ecb[h] .. 8 ecb[h] + 7; this thread
+    // gets column ec[h] = 8 ecb[h] + lane / 4 and outputs k2 = k0 + 4 r + lane % 4.
     const int q = warp & 3, g = warp >> 2;
     const int mb = (32 * g) / G::NN, k0 = ((32 * g) % G::NN) / 2;
-    const int R = mb * 128 + 32 * q + lane;  // row of Y this thread reads back
-    const int ec = R % C, ep = (R / C) & 1, eu = R / (2 * C);
+    int eu[2], ec[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int pr = 8 * mb + 2 * q + h;  // (u C/8 + c/8) of the half's groups
+        eu[h] = pr / (C / 8);
+        ec[h] = (pr % (C / 8)) * 8 + (lane >> 2);
+    }
     const int n2 = G::pt_n2(t), c = G::pt_c(t);  // the point this thread pre-filters
-    // its operand offset for spectrum u, polarisation pol of a batch is
-    // o_y + (2 u + pol) (C / 8) SBO (rows (2 u + pol) C + c, C a multiple of 8)
-    const int o_y = G::off(c, 2 * n2);
+    // its operand offsets for spectrum u of a batch: o_y + 2 u (C / 8) SBO (X)
+    // and one 8-row group further (Y), C a multiple of 8
+    const int o_y = G::off(16 * (c >> 3) + (c & 7), 2 * n2);
     // its share of the frame staging: 16-byte copies e = t + PTS i, i < SPB / 4,
     // of frame u = t / (PTS / 4) + 4 i, tile row rn2, columns 4 ch .. 4 ch + 3
     constexpr int per_row = C / 4, per_frame = PTS / 4;
@@ -254,20 +266,21 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             if (fr < 0) fr = 0;
             win[k] = unpack_p2(load_raw<2>(p.in, fr * NCH + n_pt) ^ 0x80808080u);
         }
-        // this thread's epilogue twiddles W_N^(n1 k2) 2^-12, k2 = k0 .. k0 + 15 of
-        // column ec, into its TMEM lane (the previous tile's epilogues are done
-        // with them: the barrier that ended that tile)
+        // this thread's epilogue twiddles W_N^(n1 k2) 2^-12 (column ec[h],
+        // k2 = k0 + 4 r + lane % 4) into its TMEM lane (the previous tile's
+        // epilogues are done with them: the barrier that ended that tile)
         const uint32_t ttw = tmem + ((uint32_t)(32 * q) << 16) + 2u * G::TMEM_COLS + (uint32_t)(32 * g);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
+        {
             float w[16];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const float2 v = __ldg(twsc + (size_t)x * PTS + (k0 + 8 * h + j) * C + ec);
-                w[2 * j] = v.x;
-                w[2 * j + 1] = v.y;
-            }
-            tmem_st16_wait(ttw + 16u * h, w);
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const float2 v = __ldg(twsc + (size_t)x * PTS + (k0 + 4 * r + (lane & 3)) * C + ec[h]);
+                    w[8 * h + 2 * r] = v.x;
+                    w[8 * h + 2 * r + 1] = v.y;
+                }
+            tmem_st16_wait(ttw, w);
         }
         // frames of the tile, from spectrum 0 of the chunk on (newest frame
         // of each spectrum: P - 1 frames after the spectrum's first)
@@ -285,8 +298,9 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         // Wait for batch bi's MMAs (warp-uniform answer), then its epilogue:
-        // this thread's row of D buffer bi & 1, 16 outputs k2 = k0 .. k0 + 15 of polarisation ep, column ec,
-        // spectrum eu of the batch, times W_N^(n1 k2), into the scratch.
+        // from D buffer bi & 1, per half h, both polarisations of outputs
+        // k2 = k0 + 4 r + lane % 4 (r < 4) of column ec[h], spectrum eu[h] of
+        // the batch, times W_N^(n1 k2), into the scratch as whole elements.
         // tcgen05.ld is warp-collective: every lane loads, lanes past the
         // batch's spectra skip the stores.
         auto finish = [&](int sbase, int nbb, uint32_t bi) {
@@ -294,19 +308,21 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             done = __all_sync(0xffffffffu, done);
             if (done) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (bi & 1u) * G::TMEM_COLS + (uint32_t)(32 * g);
-                float2 *z = reinterpret_cast<float2 *>(reinterpret_cast<P2 *>(p.Z) + (size_t)(sbase + eu) * NCH +
-                                                       n1_0 + ec) + ep;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    float d[16], w[16];  // 8 outputs and their twiddles
-                    tmem_ld16x2(ta + 16u * h, ttw + 16u * h, d, w);
-                    if (eu < nbb) {
+                    const uint32_t ta = tmem + ((uint32_t)(32 * q + 16 * h) << 16) + (bi & 1u) * G::TMEM_COLS +
+                                        (uint32_t)(32 * g);
+                    float d[16], w[8];  // 4 outputs of both polarisations, their twiddles
+                    tmem_ld_pairs(ta, ttw + 8u * h, d, w);
+                    if (eu[h] < nbb) {
+                        float4 *z = reinterpret_cast<float4 *>(p.Z) + (size_t)(sbase + eu[h]) * NCH + n1_0 + ec[h];
 #pragma unroll
-                        for (int j = 0; j < 8; j++) {
-                            const int k2 = k0 + 8 * h + j;
-                            st_no_l1(z + (size_t)k2 * N1 * 2, cmul(make_float2(d[2 * j], d[2 * j + 1]),
-                                                                   make_float2(w[2 * j], w[2 * j + 1])));
+                        for (int r = 0; r < 4; r++) {
+                            const int k2 = k0 + 4 * r + (lane & 3);
+                            const float2 tw = make_float2(w[2 * r], w[2 * r + 1]);
+                            const float2 xo = cmul(make_float2(d[4 * r], d[4 * r + 1]), tw);
+                            const float2 yo = cmul(make_float2(d[4 * r + 2], d[4 * r + 3]), tw);
+                            st_no_l1(z + (size_t)k2 * N1, make_float4(xo.x, xo.y, yo.x, yo.y));
                         }
                     }
                 }
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
                 uint32_t hx, lx, hy, ly;
                 split_p2(y, hx, lx, hy, ly);
                 constexpr int ou = 2 * u * (C / 8) * G::SBO;
-                const int ox = o_y + ou, oy = o_y + ou + (C / 8) * G::SBO;
+                const int ox = o_y + ou, oy = o_y + ou + G::SBO;
                 *reinterpret_cast<uint32_t *>(ahi + ox) = hx;
                 *reinterpret_cast<uint32_t *>(alo + ox) = lx;
                 *reinterpret_cast<uint32_t *>(ahi + oy) = hy;

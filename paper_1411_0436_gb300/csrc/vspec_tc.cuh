@@ -143,6 +143,31 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)
     }
 }
 
+// Two loads and their wait in one asm statement: 16 lanes x 8 columns,
+// repeated 4 times along the columns (tcgen05.ld .16x256b.x4, lanes ta ..
+// ta + 15 of the warp's quarter), and 8 columns of this thread's own lane
+// (.32x32b.x8 at tw). In the .16x256b fragment thread T holds, for
+// repetition i, lane T/4 at columns 8i + 2(T%4) and 8i + 2(T%4) + 1 (v[4i],
+// v[4i+1]) and lane T/4 + 8 at the same columns (v[4i+2], v[4i+3]).
+__device__ __forceinline__ void tmem_ld_pairs(uint32_t ta, uint32_t tw, float (&v)[16], float (&w)[8]) {
+    uint32_t r[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%25];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23])
+        : "r"(ta), "r"(tw)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+#pragma unroll
+    for (int i = 0; i < 8; i++) w[i] = __uint_as_float(r[16 + i]);
+}
+
 // Store 16 consecutive columns of this thread's TMEM lane and wait for the
 // store to complete (the same thread reads them back later).
 __device__ __forceinline__ void tmem_st16_wait(uint32_t taddr, const float (&v)[16]) {
