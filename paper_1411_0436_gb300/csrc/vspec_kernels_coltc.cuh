@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
+    // F's descriptors (fixed for the kernel)
+    const uint64_t dfhi = smem_desc(smem_addr(fhi), 128u, G::SBO), dflo = smem_desc(smem_addr(flo), 128u, G::SBO);
+    static_assert(G::smem + 1024 < (1u << 18), "descriptor start addresses: 14 bits of address / 16");
 
     // The epilogue's share of D: lane quarter q of TMEM, the 32 columns from
     // 32 g (M block mb, outputs k2 = k0 .. k0 + 15), read as two 16-lane
@@ -375,9 +378,15 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (t == 0) {
                 constexpr uint32_t idesc = instr_desc_f16(128, G::NN);
-                // small terms first: Y_lo F_hi, Y_hi F_lo, then Y_hi F_hi
-                const unsigned char *as[3] = {alo, ahi, ahi};
-                const unsigned char *bs[3] = {fhi, flo, fhi};
+                // small terms first: Y_lo F_hi, Y_hi F_lo, then Y_hi F_hi. A
+                // descriptor's start address field is the byte address / 16 and
+                // shared addresses stay below 2^18, so each operand block is its
+                // part's base descriptor plus a compile-time offset / 16 (this
+                // thread issues while the others wait at the next barrier).
+                const uint64_t dlo = smem_desc(smem_addr(alo), 128u, G::SBO);
+                const uint64_t dhi = smem_desc(smem_addr(ahi), 128u, G::SBO);
+                const uint64_t as[3] = {dlo, dhi, dhi};
+                const uint64_t bs[3] = {dfhi, dflo, dfhi};
 #pragma unroll
                 for (int m = 0; m < G::MB; m++) {
                     uint32_t acc = 0;
@@ -386,8 +395,8 @@ __global__ void __launch_bounds__(512, 1) fir_coltc_kernel(const __grid_constant
                     for (int term = 0; term < 3; term++) {
 #pragma unroll
                         for (int ks = 0; ks < G::KSTEPS; ks++) {
-                            const uint64_t ad = smem_desc(smem_addr(as[term]) + m * 16 * G::SBO + 256u * ks, 128u, G::SBO);
-                            const uint64_t bd = smem_desc(smem_addr(bs[term]) + 256u * ks, 128u, G::SBO);
+                            const uint64_t ad = as[term] + (uint64_t)((m * 16 * G::SBO + 256 * ks) >> 4);
+                            const uint64_t bd = bs[term] + (uint64_t)((256 * ks) >> 4);
                             mma_bf16(dcol, ad, bd, idesc, acc);
                             acc = 1;
                         }
