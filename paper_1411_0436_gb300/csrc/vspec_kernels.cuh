@@ -1256,6 +1256,14 @@ struct RowGrp2 {
 // column kernel's order) instead of the packed (X.re, Y.re, X.im, Y.im).
 // RING: the chunk's scratch is Zc (sc spectra), read through L2 only (ld.cg:
 // the persistent form rewrites it while CTAs run); otherwise p.Z and p.sc.
+// A 16-byte global load that does not allocate in L1.
+__device__ __forceinline__ float4 ld_no_l1(const float4 *ptr) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr));
+    return v;
+}
+
 template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool RING, typename GRP>
 __device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc_ring, int sc_ring,
                                               typename Elem<NPOL>::T *row, int x, int s, int ht, int half,
@@ -1271,10 +1279,12 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] = fir_sample<NPOL>(p, p.s0 + s, ht + 128 * q);
         } else if constexpr (ZSPLIT) {
+            // the scratch is read once: loads that do not allocate in L1, so
+            // that the rows do not push the twiddles out of it
             const float4 *zr = reinterpret_cast<const float4 *>(Zc) + (size_t)s * p.N + (size_t)x * 2048;
 #pragma unroll
             for (int q = 0; q < 16; q++) {
-                const float4 e = zr[ht + 128 * q];
+                const float4 e = ld_no_l1(zr + ht + 128 * q);
                 v[q] = make_p2(e.x, e.y, e.z, e.w);
             }
         } else if (dbg_ok(s < sc && (x + 1) * 2048 <= p.N, kDbgScratch | kDbgTile)) {
@@ -1284,6 +1294,15 @@ __device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
                     const float4 e = __ldcg(z4 + ht + 128 * q);
+                    v[q] = P2{make_float2(e.x, e.y), make_float2(e.z, e.w)};
+                }
+            } else if constexpr (NPOL == 2) {
+                // read once: loads that do not allocate in L1, so that the
+                // rows do not push the twiddles out of it
+                const float4 *z4 = reinterpret_cast<const float4 *>(zr);
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const float4 e = ld_no_l1(z4 + ht + 128 * q);
                     v[q] = P2{make_float2(e.x, e.y), make_float2(e.z, e.w)};
                 }
             } else {
