@@ -173,6 +173,24 @@ __device__ __forceinline__ P2 unpack_p2(uint32_t wx) {
     return P2{__fadd2_rn(r, bias), __fadd2_rn(i, bias)};
 }
 
+// Global loads that do not allocate in L1 (data read once, such as the
+// chunk scratch, so that it does not push reused tables out of L1).
+__device__ __forceinline__ float4 ld_no_l1(const float4 *ptr) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr));
+    return v;
+}
+__device__ __forceinline__ float2 ld_no_l1(const float2 *ptr) {
+    float2 v;
+    asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
+    return v;
+}
+__device__ __forceinline__ P2 ld_no_l1(const P2 *ptr) {
+    const float4 e = ld_no_l1(reinterpret_cast<const float4 *>(ptr));
+    return P2{make_float2(e.x, e.y), make_float2(e.z, e.w)};
+}
+
 template <int NPOL> __device__ __forceinline__ uint32_t load_raw(const int8_t *in, long long m);
 template <> __device__ __forceinline__ uint32_t load_raw<2>(const int8_t *in, long long m) {
     return __ldg(reinterpret_cast<const unsigned int *>(in) + m);
@@ -1036,7 +1054,7 @@ __device__ __forceinline__ void row_butterfly(const RowParams &p, int x, typenam
     } else if (first) {
         const T *zr = Zs + (size_t)(x * p.RB + r) * p.N1;
 #pragma unroll
-        for (int q = 0; q < R; q++) v[q] = zr[base + q * ps.m];
+        for (int q = 0; q < R; q++) v[q] = ld_no_l1(zr + base + q * ps.m);  // read once
     } else {
 #pragma unroll
         for (int q = 0; q < R; q++) v[q] = row[pad16(base + q * ps.m)];
@@ -1256,14 +1274,6 @@ struct RowGrp2 {
 // column kernel's order) instead of the packed (X.re, Y.re, X.im, Y.im).
 // RING: the chunk's scratch is Zc (sc spectra), read through L2 only (ld.cg:
 // the persistent form rewrites it while CTAs run); otherwise p.Z and p.sc.
-// A 16-byte global load that does not allocate in L1.
-__device__ __forceinline__ float4 ld_no_l1(const float4 *ptr) {
-    float4 v;
-    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr));
-    return v;
-}
-
 template <int NPOL, bool KAHAN, bool FIR, bool ZSPLIT, bool RING, typename GRP>
 __device__ __forceinline__ void row2048_first(const RowParams &p, const void *Zc_ring, int sc_ring,
                                               typename Elem<NPOL>::T *row, int x, int s, int ht, int half,
