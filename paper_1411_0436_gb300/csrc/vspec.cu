@@ -795,9 +795,13 @@ vspec_status build_plan(vspec_plan *p) {
         p->tc_cols = true;
     }
     if (p->fir_b) p->formA = "none";
+    // dual-pol 4096-point rows without a pre-filter in kernel B, compensated
+    // sums or tensor-core rows: four radix-8 passes (row4096_kernel)
+    const bool row4096 = N1 == 4096 && p->npol == 2 && !p->fir_b &&
+                         !(p->flags & (VSPEC_PLAN_KAHAN | VSPEC_PLAN_TENSOR | VSPEC_PLAN_TENSOR_INT8));
     const std::vector<int> rA = (tcfir || coltc) ? std::vector<int>{N2} : colreg ? r_colreg : coldir ? r_coldir
                                                                                : radix_list(e2, maxbitsA),
-                           rB = radix_list(e1);
+                           rB = row4096 ? std::vector<int>{8, 8, 8, 8} : radix_list(e1);
     int twA_n = 0, twB_n = 0;
     p->passA = make_passes(N2, rA, &twA_n);
     p->passB = make_passes(N1, rB, &twB_n);
@@ -867,6 +871,14 @@ vspec_status build_plan(vspec_plan *p) {
         p->smemB = 2 * (size_t)kRow2048Stride * elem;
         p->formB = "row2048";
         p->fold2048 = N2 >= 16 && !p->kahan;
+    }
+    // 4096-point rows (radix 8, 8, 8, 8): one spectrum per pass sequence,
+    // register accumulators
+    if (row4096 && !p->tc && p->RB == 1 && p->passB.size() == 4) {
+        p->kernelB = (const void *)vspec::row4096_kernel<false>;
+        p->TB = 512;
+        p->smemB = (size_t)vspec::kRow4096Stride * elem;
+        p->formB = "row4096";
     }
 
     // the persistent ring form: the register-column kernel A and the paired

@@ -1443,6 +1443,107 @@ __global__ void __launch_bounds__(256, KAHAN ? 1 : 2) row2048_kernel(const __gri
     }
 }
 
+// Kernel B for 4096-point rows (dual-pol, no pre-filter; 2^19 PFB plans):
+// four radix-8 DIF passes over one spectrum's row at a time, 512 threads with
+// one butterfly each per pass (pass with block length L: block b, butterfly j
+// over positions b L + j + (L / 8) q, outputs times W_L^(j q)). Thread t
+// computes outputs 8t .. 8t+7 of the last pass, so its eight channels'
+// accumulators stay in registers, with the two-level sums of the 2048-point
+// kernel. The row uses the pad8 layout: in every pass the 8 threads of a
+// 16-byte phase touch 8 different bank groups.
+constexpr int kRow4096Stride = 4096 + 4096 / 8;
+
+template <bool ZSPLIT = false>
+__global__ void __launch_bounds__(512, 1) row4096_kernel(const __grid_constant__ RowParams p) {
+    using A = float4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P2 *row = reinterpret_cast<P2 *>(smem_raw);  // one row, pad8 layout
+    const int t = threadIdx.x;
+    const Span sp = block_span(p.tiles, p.sc);
+    for (long long f = sp.lo; f < sp.hi;) {
+        const int x = (int)(f / p.sc);  // row tile
+        const long long base = (long long)x * p.sc;
+        const int s_beg = (int)(f - base);
+        const int s_end = (int)(min(sp.hi, base + p.sc) - base);
+        f = base + s_end;
+
+        A acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // add the registers into this block's slot (thread t holds positions
+        // 8t .. 8t+7 of row tile x); `store`: the slot's first write this call
+        auto flush = [&](bool store) {
+            if (!dbg_ok(span_slot(p.tiles, p.sc, x) < p.slots && (x + 1) * 4096 <= p.N, kDbgSlot)) return;
+            A *part = reinterpret_cast<A *>(p.partial) + (size_t)span_slot(p.tiles, p.sc, x) * p.N +
+                      (size_t)x * 4096 + 8 * t;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if (store) part[q] = acc[q];
+                else atomicAdd(part + q, acc[q]);  // in L2; one writer per entry, in program order
+            }
+        };
+        bool first = p.store != 0;
+        for (int s = s_beg; s < s_end; s++) {
+            // pass 1: block length 4096, butterfly j = t over positions t + 512 q
+            {
+                P2 v[8];
+                if (dbg_ok(s < p.sc && (x + 1) * 4096 <= p.N, kDbgScratch | kDbgTile)) {
+                    const float4 *zr = reinterpret_cast<const float4 *>(p.Z) + (size_t)s * p.N + (size_t)x * 4096;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const float4 e = ld_no_l1(zr + t + 512 * q);  // read once
+                        v[q] = ZSPLIT ? make_p2(e.x, e.y, e.z, e.w) : P2{make_float2(e.x, e.y), make_float2(e.z, e.w)};
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; q++) v[q] = P2{};
+                }
+                Dft<8>::run(v);
+                const float2 *tw = p.twB + p.pass[0].off + t * 7;
+#pragma unroll
+                for (int q = 1; q < 8; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+#pragma unroll
+                for (int q = 0; q < 8; q++) row[pad8(t + 512 * q)] = v[q];
+            }
+            __syncthreads();
+            // passes 2 and 3: block length 512 (b = t / 64, j = t % 64) and 64 (b = t / 8, j = t % 8)
+#pragma unroll
+            for (int k = 1; k < 3; k++) {
+                const int m = k == 1 ? 64 : 8;
+                const int j = t & (m - 1), bbase = (t / m) * (8 * m) + j;
+                P2 v[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) v[q] = row[pad8(bbase + m * q)];
+                Dft<8>::run(v);
+                const float2 *tw = p.twB + p.pass[k].off + j * 7;
+#pragma unroll
+                for (int q = 1; q < 8; q++) v[q] = cmul(v[q], __ldg(tw + q - 1));
+#pragma unroll
+                for (int q = 0; q < 8; q++) row[pad8(bbase + m * q)] = v[q];
+                __syncthreads();
+            }
+            // pass 4: block length 8, outputs 8t .. 8t+7: detection and accumulation
+            {
+                P2 v[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) v[q] = row[pad8(8 * t + q)];
+                Dft<8>::run(v);
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc_add<2>(acc[q], v[q]);
+            }
+            // end of a register run with more spectra to come: into the slot
+            if (((s - s_beg) % kRow2048Run) == kRow2048Run - 1 && s + 1 < s_end) {
+                flush(first);
+                first = false;
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();  // the row is free for the next spectrum
+        }
+        flush(first);
+    }
+}
+
 // ------------------------------------------------------------ sub-bands --
 // Eight-sub-band modes (16 FFTs in parallel, §4): the input interleaves nsub
 // sub-bands per time sample, [time][sub][pol][re, im]. This kernel copies a

@@ -628,7 +628,7 @@ def test_fused_assist_shares_match_oracle(oracle_mod, cfg):
     ((524288, 1, 2, DIRECT, WIN_RECT, 0), ("two-kernel", "A=coldir", "N2=256", "B=row2048")),  # c3
     ((131072, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N2=64", "C=8", "B=row2048")),         # c4
     ((262144, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N2=128", "C=4")),
-    ((524288, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N1=4096", "B=general")),
+    ((524288, 8, 2, PFB, WIN_HANN, 0), ("A=colreg", "N1=4096", "B=row4096")),
     ((1 << 20, 8, 2, PFB, WIN_HANN, 0), ("A=gather", "N1=2048")),
     ((1024, 8, 1, PFB, WIN_HANN, 0), ("A=none", "fir-in-B", "B=general")),              # c1
     ((65536, 4, 1, PFB, WIN_HANN, 0), ("A=general",)),
